@@ -1,0 +1,103 @@
+"""Pins of the oracle's FISTA driver: special cases with closed-form minimisers,
+optimality (KKT) conditions, and ISTA's monotone descent."""
+import numpy as np
+import pytest
+
+from oracle import rihv_oracle as O
+from tests import _brute as B
+
+IDENT = O.Optics(nx=16, ny=12, nz=1, wavelength=632.8e-9, pitch=10e-6, z0=0.0, dz=1e-4)
+SMALL = O.Optics(nx=16, ny=16, nz=4, wavelength=632.8e-9, pitch=10e-6, z0=2e-3, dz=300e-6)
+
+
+def _hologram(optics, seed):
+    rng = np.random.default_rng(seed)
+    a = np.zeros(optics.shape)
+    for _ in range(6):
+        k, j, i = (rng.integers(0, s) for s in optics.shape)
+        a[k, max(j - 1, 0):j + 2, max(i - 1, 0):i + 2] = 1.0
+    b = 2 * O.forward(a, optics).real + 0.01 * rng.standard_normal((optics.ny, optics.nx))
+    return b
+
+
+def test_identity_operator_lasso_closed_form():
+    """nz = 1 at z = 0 gives H = I, so min ||x - b||^2 + lam ||x||_1 has the
+    closed form x = soft_{lam/2}(b); FISTA reaches it (here in one step, since
+    tau = 1/2 makes v = b)."""
+    rng = np.random.default_rng(0)
+    b = rng.standard_normal((IDENT.ny, IDENT.nx))
+    lam = 0.6
+    x, _ = O.fista(b, IDENT, lam, 0.0, iters=5, n_inner=0)
+    ref = np.sign(b) * np.maximum(np.abs(b) - lam / 2, 0)
+    np.testing.assert_allclose(x[0], ref, atol=1e-12)
+
+
+def test_identity_operator_tv_matches_brute_force():
+    """With H = I and lam_l1 = 0, the minimiser of ||x - b||^2 + lam_tv TV(x) is
+    prox_{(lam_tv/2) TV}(b); compared with the certified primal-dual solve."""
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal((IDENT.ny, IDENT.nx))
+    lam_tv = 0.5
+    x, _ = O.fista(b, IDENT, 0.0, lam_tv, iters=3, n_inner=3000)
+    ref, gap = B.fused_lasso_prox_cp(b[None].astype(complex), lam_tv / 2, 0.0, 3,
+                                     max_iter=20000, gap_tol=1e-14)
+    assert np.linalg.norm(x - ref) <= np.sqrt(2 * gap) + 1e-6
+
+
+def test_lasso_kkt_conditions_at_convergence():
+    """After many FISTA iterations with lam_tv = 0, the subgradient optimality
+    conditions of min ||Hx - b||^2 + lam ||x||_1 hold: g = 2 H^H(Hx - b) equals
+    -lam x/|x| on the support and has |g| <= lam off it."""
+    b = _hologram(SMALL, 2)
+    lam = 0.5
+    x, _ = O.fista(b, SMALL, lam, 0.0, iters=3000, n_inner=0)
+    g = O.grad_data(x, b, SMALL)
+    on = np.abs(x) > 1e-9
+    assert on.sum() > 0
+    np.testing.assert_allclose(g[on], -lam * x[on] / np.abs(x[on]), atol=2e-6)
+    assert np.abs(g[~on]).max() <= lam * (1 + 1e-6)
+
+
+def test_ista_monotone_without_tv():
+    """ISTA with an exact prox never increases the objective."""
+    b = _hologram(SMALL, 3)
+    vals = [O.objective(np.zeros(SMALL.shape), b, SMALL, 0.3, 0.0)]
+    x = None
+    for k in range(1, 16):
+        x, _ = O.fista(b, SMALL, 0.3, 0.0, iters=1, n_inner=0, accelerate=False, x0=x)
+        vals.append(O.objective(x, b, SMALL, 0.3, 0.0))
+    assert all(v1 <= v0 + 1e-12 * abs(v0) for v0, v1 in zip(vals, vals[1:]))
+
+
+def test_ista_monotone_with_converged_tv_prox():
+    b = _hologram(SMALL, 4)
+    lam1, lamtv = 0.2, 0.3
+    x = None
+    vals = [O.objective(np.zeros(SMALL.shape), b, SMALL, lam1, lamtv)]
+    for k in range(8):
+        x, _ = O.fista(b, SMALL, lam1, lamtv, iters=1, n_inner=400, accelerate=False, x0=x)
+        vals.append(O.objective(x, b, SMALL, lam1, lamtv))
+    assert all(v1 <= v0 + 1e-9 * abs(v0) for v0, v1 in zip(vals, vals[1:]))
+
+
+@pytest.mark.parametrize("restart", [True, False])
+def test_fista_reaches_ista_fixed_point_faster(restart):
+    """FISTA and many ISTA iterations approach the same minimiser (lasso case),
+    and FISTA gets closer in the same number of iterations."""
+    b = _hologram(SMALL, 5)
+    lam = 0.4
+    ref, _ = O.fista(b, SMALL, lam, 0.0, iters=4000, n_inner=0)
+    xf, _ = O.fista(b, SMALL, lam, 0.0, iters=60, n_inner=0, restart=restart)
+    xi, _ = O.fista(b, SMALL, lam, 0.0, iters=60, n_inner=0, accelerate=False)
+    assert np.linalg.norm(xf - ref) < np.linalg.norm(xi - ref)
+
+
+def test_objective_trace_and_warm_start():
+    b = _hologram(SMALL, 6)
+    x, tr = O.fista(b, SMALL, 0.2, 0.1, iters=20, n_inner=10, check_every=5)
+    assert [k for k, _ in tr] == [5, 10, 15, 20]
+    assert tr[-1][1] < O.objective(np.zeros(SMALL.shape), b, SMALL, 0.2, 0.1)
+    # Warm start from the answer of a long run barely moves.
+    xl, _ = O.fista(b, SMALL, 0.2, 0.0, iters=3000, n_inner=0)
+    xw, _ = O.fista(b, SMALL, 0.2, 0.0, iters=5, n_inner=0, x0=xl)
+    assert np.linalg.norm(xw - xl) < 1e-6 * np.linalg.norm(xl)
