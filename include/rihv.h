@@ -1,0 +1,162 @@
+/*
+ * rihv.h - C ABI of the GB300 fused-lasso holographic volume reconstruction
+ * library (librihv.so).
+ *
+ * Method: "Regularized Inverse Holographic Volume Reconstruction for 3D
+ * Particle Tracking" (arXiv 1904.04884), Section 2. The library recovers a
+ * complex volume x [nz][ny][nx] from one real hologram b [ny][nx] by solving
+ *     min_x ||H x - b||_2^2 + lambda_l1 ||x||_1 + lambda_tv ||x||_TV
+ * with FISTA, where H is the linearised angular-spectrum forward model.
+ *
+ * Conventions shared by every entry point
+ *  - Volumes are complex64 (interleaved re, im float32), C order [nz][ny][nx],
+ *    x fastest. Holograms are float32 [ny][nx]. Spectral/2D fields are
+ *    complex64 [ny][nx].
+ *  - Plane j lies at depth z_j = z0 + j*dz. Frequencies are in FFT order,
+ *    f_x = k_x / (nx * pitch). The transfer function of plane j is
+ *    H_j(f) = exp(i 2 pi z_j sqrt(1/wavelength^2 - f_x^2 - f_y^2)) on the
+ *    propagating band and 0 for evanescent frequencies; it is generated inside
+ *    the kernels, never stored.
+ *  - Supported sizes: nx, ny in {n = 2^a * 3^b : 16 <= n <= 1024, a >= 3,
+ *    b <= 1}; 1 <= nz <= 4096. Other sizes return RIHV_ERR_UNSUPPORTED_SIZE.
+ *  - Pointers marked "device" must be CUDA device memory of the current
+ *    device, 16-byte aligned and not overlapping each other. Pointers marked
+ *    "host or device" may also be host memory; the library then copies
+ *    through its own staging buffers (the call synchronises the stream).
+ *  - All work is queued on the handle's stream (rihv_set_stream; default: the
+ *    legacy default stream). Calls return once the work is queued unless they
+ *    say otherwise. The caller owns every pointer it passes; the library owns
+ *    its scratch, which rihv_create allocates and rihv_destroy frees. No call
+ *    other than rihv_create and rihv_detect (first use) allocates memory.
+ *  - Errors: every call returns a status; arguments are checked before any
+ *    launch. rihv_last_error() gives a message for the last failing call on
+ *    the handle. A handle is not thread safe.
+ */
+#ifndef RIHV_H
+#define RIHV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rihv_ctx* rihv_handle;
+
+typedef enum {
+  RIHV_OK = 0,
+  RIHV_ERR_INVALID_ARG = 1,      /* bad pointer, size, alignment or value    */
+  RIHV_ERR_CUDA = 2,             /* a CUDA runtime call failed               */
+  RIHV_ERR_OOM = 3,              /* device allocation failed                 */
+  RIHV_ERR_NONFINITE = 4,        /* objective or a norm became NaN/Inf       */
+  RIHV_ERR_TIMEOUT = 5,          /* a bounded device wait gave up            */
+  RIHV_ERR_UNSUPPORTED_SIZE = 6  /* grid size outside the supported set      */
+} rihv_status;
+
+/* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
+ * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0. */
+typedef struct {
+  int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
+                        TV prox paragraph restricts TV to planes)            */
+  int restart;       /* 1: gradient restart (O'Donoghue-Candes) on           */
+  int accelerate;    /* 1: FISTA momentum; 0: ISTA (t == 1)                  */
+  int n_inner;       /* TV dual gradient-projection steps per prox (>= 0)    */
+  int check_every;   /* evaluate F(x_k) every M iterations (0: never)        */
+  double tol;        /* with f_star > 0: stop at the first check where       */
+  double f_star;     /*   F(x_k) <= f_star * (1 + tol)                       */
+} rihv_options;
+
+/* One detected particle (Section 2, segmentation paragraph). */
+typedef struct {
+  double cx, cy, cz;  /* |x|-weighted centroid in voxel units (x, y, z)     */
+  double weight;      /* sum of |x| over the component                       */
+  int64_t first;      /* smallest linear voxel index (k*ny + j)*nx + i       */
+  int32_t nvox;       /* voxels in the component                             */
+  int32_t pad_;
+} rihv_particle;
+
+/* Fills *opt with the defaults listed above. */
+void rihv_default_options(rihv_options* opt);
+
+/* Creates a handle for one grid and optics (lengths in metres; wavelength is
+ * the illumination wavelength, not a regularisation weight). Allocates all
+ * scratch for forward/adjoint/prox/solve on the current CUDA device.
+ * Returns RIHV_ERR_UNSUPPORTED_SIZE for sizes outside the supported set,
+ * RIHV_ERR_INVALID_ARG for non-positive wavelength/pitch or a null *out,
+ * RIHV_ERR_OOM if scratch does not fit. */
+rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
+                        double z0, double dz, rihv_handle* out);
+
+/* Synchronises the handle's stream, frees its scratch and the handle. */
+rihv_status rihv_destroy(rihv_handle h);
+
+/* Sets the cudaStream_t (passed as void*) all later calls queue on. */
+rihv_status rihv_set_stream(rihv_handle h, void* stream);
+
+/* Sets solver options (copied). Invalid values return RIHV_ERR_INVALID_ARG. */
+rihv_status rihv_set_options(rihv_handle h, const rihv_options* opt);
+
+/* Forward model (Section 2, linearised model b_hat = H x):
+ * out = sum_j F^-1 (H_j . F x_j).
+ * x: device complex64 [nz][ny][nx]; out: device complex64 [ny][nx]. */
+rihv_status rihv_forward(rihv_handle h, const void* x, void* out);
+
+/* Adjoint of the forward model ("reverse propagation", Section 2):
+ * out_j = F^-1 (conj(H_j) . F r) for every plane j.
+ * r: device complex64 [ny][nx]; out: device complex64 [nz][ny][nx]. */
+rihv_status rihv_adjoint(rihv_handle h, const void* r, void* out);
+
+/* Fused-lasso proximal operator (Section 2, FL paragraph): the TV prox of v
+ * with weight t_tv by `inner_iters` Beck-Teboulle dual gradient-projection
+ * steps from p = 0, then soft thresholding with t_l1. t_l1 and t_tv are
+ * already multiplied by the step size. Uses the handle's tv_dims.
+ * v, x_out: device complex64 [nz][ny][nx]. */
+rihv_status rihv_prox_fused_lasso(rihv_handle h, const void* v, float t_l1, float t_tv,
+                                  int inner_iters, void* x_out);
+
+/* Fused-lasso FISTA (Section 2, FISTA paragraph and shrinkage step) for
+ * `iters` iterations with step 1/L, L = 2 max_f sum_j |H_j(f)|^2.
+ * hologram: host or device float32 [ny][nx].
+ * x0_or_null: host or device complex64 volume to start from, or NULL for 0.
+ * x_out: host or device complex64 [nz][ny][nx], receives x_iters.
+ * objective_trace_or_null: host or device double array with one slot per
+ *   objective check (iters / check_every entries), or NULL.
+ * If *iters_done is non-NULL it receives the iterations actually run (fewer
+ * than iters only when the f_star stop test fired). With host output
+ * pointers or an active stop test the call returns after the stream
+ * finishes; otherwise it returns once the work is queued. */
+rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, float lambda_tv,
+                       int iters, const void* x0_or_null, void* x_out,
+                       double* objective_trace_or_null, int* iters_done);
+
+/* Particle detection on a volume (Section 2, segmentation paragraph):
+ * voxels with |x| > rel_thresh * max|x|, 26-connected components, components
+ * of <= min_vox voxels dropped, |x|-weighted centroids. Particles are written
+ * to host array `out` (capacity max_out) in order of their smallest linear
+ * voxel index; *n_out receives the number found (which may exceed max_out;
+ * only max_out are written). x: device complex64 [nz][ny][nx]. Synchronises
+ * the stream. The first call allocates the labelling scratch. */
+rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
+                        rihv_particle* out, int max_out, int* n_out);
+
+/* Per-stage timing. When on, the library records CUDA events around its
+ * stages on the handle's stream; rihv_stage_times then returns accumulated
+ * milliseconds and launch counts per stage (after synchronising the stream)
+ * and resets them. Stages, in order: 0 forward, 1 adjoint+gradient step,
+ * 2 TV dual steps, 3 finalize (soft threshold, momentum, restart), 4 objective,
+ * 5 detection. n is the capacity of both arrays (up to 6 are written). */
+rihv_status rihv_set_profiling(rihv_handle h, int on);
+rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int n);
+
+/* Step size tau = 1/L used by rihv_solve (host-computed in FP64). */
+rihv_status rihv_step_size(rihv_handle h, double* tau);
+
+/* Message for the last failing call on h (or a global message if h is NULL). */
+const char* rihv_last_error(rihv_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIHV_H */

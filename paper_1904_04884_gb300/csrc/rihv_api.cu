@@ -1,0 +1,705 @@
+// C ABI of librihv: handle, scratch, transfer-function phase tables and the
+// drivers that sequence the kernels of the forward model, its adjoint, the
+// fused-lasso prox and FISTA (Section 2 of arXiv 1904.04884).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rihv_internal.cuh"
+
+using namespace rihv;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kNumStages = 6;
+enum Stage { ST_FORWARD = 0, ST_ADJOINT = 1, ST_TV = 2, ST_FINAL = 3, ST_OBJECTIVE = 4, ST_DETECT = 5 };
+constexpr int kEventPool = 8192;
+
+bool supported_n(int n) {
+  if (n < 16 || n > kMaxN) return false;
+  int m = n, twos = 0, threes = 0;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  while (m % 3 == 0) { m /= 3; ++threes; }
+  return m == 1 && twos >= 3 && threes <= 1;
+}
+
+FftPlan make_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  int m = n;
+  while (m % 8 == 0) { p.radix[p.npass++] = 8; m /= 8; }
+  if (m % 4 == 0) { p.radix[p.npass++] = 4; m /= 4; }
+  if (m % 2 == 0) { p.radix[p.npass++] = 2; m /= 2; }
+  if (m % 3 == 0) { p.radix[p.npass++] = 3; m /= 3; }
+  return p;
+}
+
+double frac(double x) { return x - std::floor(x); }
+
+uint32_t to_cycles32(double f) {
+  // f in [0, 1) -> nearest multiple of 2^-32, wrapped
+  const double s = std::floor(f * 4294967296.0 + 0.5);
+  return static_cast<uint32_t>(static_cast<uint64_t>(s) & 0xFFFFFFFFull);
+}
+
+double fft_freq(int k, int n, double pitch) {
+  const int kk = (k < n / 2) ? k : k - n;   // even n
+  return static_cast<double>(kk) / (n * pitch);
+}
+
+}  // namespace
+
+struct rihv_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  double wavelength = 0, pitch = 0, z0 = 0, dz = 0;
+  size_t nxy = 0, nvox = 0;
+  cudaStream_t stream = nullptr;
+  rihv_options opt{};
+  int device = 0;
+  int groups = 1, zpg = 1;
+  int tv_zchunk = 32;
+  double tau = 0;
+  FftPlan plan_x{}, plan_y{};
+  std::string err;
+
+  // device buffers
+  float2* tw_x = nullptr;
+  float2* tw_y = nullptr;
+  uint2* phase = nullptr;
+  float* amp = nullptr;
+  float2* inter = nullptr;     // strip-major intermediate [nz][nx/W][ny][W]
+  float2* partial = nullptr;   // [groups][ny][nx]
+  float2* spec = nullptr;      // [ny][nx] spectrum sum / residual spectrum
+  float2* bhat = nullptr;      // [ny][nx] F b
+  float* holo = nullptr;       // [ny][nx]
+  float2* x = nullptr;         // volumes
+  float2* y = nullptr;
+  float2* v = nullptr;
+  float2* pa[3] = {nullptr, nullptr, nullptr};
+  float2* pb[3] = {nullptr, nullptr, nullptr};
+  DevScalars* sc = nullptr;
+  RedWork red{};
+  double* trace = nullptr;     // device objective trace
+  int trace_cap = 0;
+  int* det_err = nullptr;
+  DetectWork det{};
+  std::vector<void*> allocs;
+
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec { int stage; int launches; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  double stage_ms[kNumStages] = {0};
+  long long stage_launches[kNumStages] = {0};
+};
+
+namespace {
+
+rihv_status fail(rihv_ctx* h, rihv_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  g_last_error = buf;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, RIHV_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+#define CKS(call)                      \
+  do {                                 \
+    rihv_status s_ = (call);           \
+    if (s_ != RIHV_OK) return s_;      \
+  } while (0)
+
+template <typename T>
+rihv_status dalloc(rihv_ctx* h, T** p, size_t count) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RIHV_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  h->allocs.push_back(ptr);
+  *p = static_cast<T*>(ptr);
+  return RIHV_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+rihv_status check_dev(rihv_ctx* h, const void* p, const char* name) {
+  if (!p) return fail(h, RIHV_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!aligned16(p)) return fail(h, RIHV_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  if (!is_device_ptr(p)) return fail(h, RIHV_ERR_INVALID_ARG, "%s is not device memory", name);
+  return RIHV_OK;
+}
+
+// ---- profiling -------------------------------------------------------------
+struct StageScope {
+  rihv_ctx* h;
+  int stage;
+  int launches;
+  cudaEvent_t a = nullptr;
+  StageScope(rihv_ctx* hh, int st, int nl) : h(hh), stage(st), launches(nl) {
+    if (!h->prof) return;
+    if (h->ev_used + 2 > h->ev_pool.size()) flush();
+    a = h->ev_pool[h->ev_used++];
+    cudaEventRecord(a, h->stream);
+  }
+  ~StageScope() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = h->ev_pool[h->ev_used++];
+    cudaEventRecord(b, h->stream);
+    h->recs.push_back({stage, launches, a, b});
+  }
+  void flush() {
+    cudaStreamSynchronize(h->stream);
+    for (auto& r : h->recs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      h->stage_ms[r.stage] += ms;
+      h->stage_launches[r.stage] += r.launches;
+    }
+    h->recs.clear();
+    h->ev_used = 0;
+  }
+};
+
+// ---- stage drivers ----------------------------------------------------------
+RowArgs row_args(rihv_ctx* h, const void* src, float2* dst, int nz) {
+  RowArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = nz;
+  a.scale = 1.f;
+  a.plan = h->plan_x;
+  a.tw = h->tw_x;
+  return a;
+}
+
+ColArgs col_args(rihv_ctx* h, const float2* src, float2* dst) {
+  ColArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.phase = h->phase;
+  a.amp = h->amp;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.z_per_group = h->zpg;
+  a.scale = 1.f;
+  a.plan = h->plan_y;
+  a.tw = h->tw_y;
+  return a;
+}
+
+// Spectrum of the modelled hologram S = sum_j H_j F x_j; with bhat, the
+// residual spectrum R = S - F b and ||Hx - b||^2 -> sc->rnorm2.
+rihv_status forward_spectrum(rihv_ctx* h, const float2* xin, const float2* bhat, float2* out) {
+  StageScope sc(h, ST_FORWARD, 3);
+  CK(launch_rows(0, ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE, row_args(h, xin, h->inter, h->nz),
+                 h->stream));
+  CK(launch_cols(COL_FWD_ZSUM, col_args(h, h->inter, h->partial), h->groups, h->stream));
+  CK(launch_zsum(h->partial, h->groups, bhat, out, h->nx, h->ny, h->sc, h->red, h->stream));
+  return RIHV_OK;
+}
+
+// Per-plane inverse propagation of the spectrum `spec`: with grad, out =
+// y - scale * F^-1(conj(H_j) spec); otherwise out = scale * F^-1(conj(H_j) spec).
+rihv_status adjoint_planes(rihv_ctx* h, const float2* spec, const float2* y, float2* out,
+                           float scale, bool grad) {
+  StageScope sc(h, ST_ADJOINT, 2);
+  CK(launch_cols(COL_ADJ_GEN, col_args(h, spec, h->inter), h->groups, h->stream));
+  RowArgs ra = row_args(h, h->inter, out, h->nz);
+  ra.scale = scale;
+  ra.y = y;
+  CK(launch_rows(1, ROW_IN_STRIP, ROW_OUT_C64, grad ? ROW_EPI_GRAD : ROW_EPI_SCALE, ra, h->stream));
+  return RIHV_OK;
+}
+
+// 2D FFT of one plane (complex or real row-major input) -> row-major spectrum.
+rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) {
+  CK(launch_rows(0, real_in ? ROW_IN_F32 : ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE,
+                 row_args(h, src, h->inter, 1), h->stream));
+  CK(launch_cols(COL_PLAIN_FWD, col_args(h, h->inter, out), 1, h->stream));
+  return RIHV_OK;
+}
+
+// K dual steps; returns the buffer set holding the final p.
+rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
+  StageScope sc(h, ST_TV, k);
+  TvArgs a{};
+  a.v = v;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.dims = h->opt.tv_dims;
+  a.zchunk = h->tv_zchunk;
+  a.mu = mu;
+  a.step = 1.f / (4.f * a.dims * mu);
+  float2** src = h->pb;
+  float2** dst = h->pa;
+  for (int it = 0; it < k; ++it) {
+    for (int c = 0; c < 3; ++c) {
+      a.pin[c] = src[c];
+      a.pout[c] = dst[c];
+    }
+    CK(launch_tv_step(it == 0, a, h->stream));
+    std::swap(src, dst);
+  }
+  *pfinal = src;
+  return RIHV_OK;
+}
+
+rihv_status prox_into(rihv_ctx* h, const float2* v, float t_l1, float t_tv, int k, int mode,
+                      float2* x_out) {
+  float2* const* pf = nullptr;
+  const bool tv = (t_tv > 0.f && k > 0);
+  if (tv) CKS(tv_steps(h, v, t_tv, k, &pf));
+  StageScope sc(h, ST_FINAL, mode == FIN_FISTA ? 2 : 1);
+  FinArgs f{};
+  f.v = v;
+  for (int c = 0; c < 3; ++c) f.p[c] = tv ? pf[c] : nullptr;
+  f.x_prev = h->x;
+  f.y = h->y;
+  f.x_out = x_out;
+  f.y_out = h->y;
+  f.nx = h->nx;
+  f.ny = h->ny;
+  f.nz = h->nz;
+  f.dims = h->opt.tv_dims;
+  f.mu = tv ? t_tv : 0.f;
+  f.kappa = t_l1;
+  f.sc = h->sc;
+  f.w = h->red;
+  CK(launch_finalize(mode, f, h->stream));
+  if (mode == FIN_FISTA) CK(launch_restart_fixup(x_out, h->y, h->nvox, h->sc, h->stream));
+  return RIHV_OK;
+}
+
+rihv_status copy_in(rihv_ctx* h, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+  return RIHV_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+void rihv_default_options(rihv_options* o) {
+  if (!o) return;
+  o->tv_dims = 3;
+  o->restart = 1;
+  o->accelerate = 1;
+  o->n_inner = 20;
+  o->check_every = 10;
+  o->tol = 0.0;
+  o->f_star = 0.0;
+}
+
+const char* rihv_last_error(rihv_handle h) {
+  return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch, double z0,
+                        double dz, rihv_handle* out) {
+  rihv_ctx* h = nullptr;
+  if (!out) return fail(nullptr, RIHV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!supported_n(nx) || !supported_n(ny) || nz < 1 || nz > 4096)
+    return fail(nullptr, RIHV_ERR_UNSUPPORTED_SIZE,
+                "unsupported size %dx%dx%d (nx, ny in 2^a 3^b, 16..1024, a>=3, b<=1; 1<=nz<=4096)",
+                nx, ny, nz);
+  if (!(wavelength > 0) || !(pitch > 0) || !std::isfinite(z0) || !std::isfinite(dz))
+    return fail(nullptr, RIHV_ERR_INVALID_ARG, "wavelength and pitch must be > 0, z0/dz finite");
+  h = new (std::nothrow) rihv_ctx();
+  if (!h) return fail(nullptr, RIHV_ERR_OOM, "host allocation failed");
+  h->nx = nx; h->ny = ny; h->nz = nz;
+  h->wavelength = wavelength; h->pitch = pitch; h->z0 = z0; h->dz = dz;
+  h->nxy = static_cast<size_t>(nx) * ny;
+  h->nvox = h->nxy * nz;
+  rihv_default_options(&h->opt);
+  h->plan_x = make_plan(nx);
+  h->plan_y = make_plan(ny);
+  cudaGetDevice(&h->device);
+
+  // z-groups of the column passes: about 4 CTAs per SM in total.
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int strips = nx / kStrip;
+  int g = (4 * sms + strips - 1) / strips;
+  g = std::max(1, std::min(g, nz));
+  h->zpg = (nz + g - 1) / g;
+  h->groups = (nz + h->zpg - 1) / h->zpg;
+
+  auto cleanup = [&](rihv_status st) {
+    rihv_destroy(h);
+    return st;
+  };
+  rihv_status st;
+#define AL(ptr, n) \
+  if ((st = dalloc(h, &(ptr), (n))) != RIHV_OK) return cleanup(st)
+  AL(h->tw_x, nx);
+  AL(h->tw_y, ny);
+  AL(h->phase, h->nxy);
+  AL(h->amp, h->nxy);
+  AL(h->inter, h->nvox);
+  AL(h->partial, h->nxy * h->groups);
+  AL(h->spec, h->nxy);
+  AL(h->bhat, h->nxy);
+  AL(h->holo, h->nxy);
+  AL(h->x, h->nvox);
+  AL(h->y, h->nvox);
+  AL(h->v, h->nvox);
+  for (int c = 0; c < 3; ++c) {
+    AL(h->pa[c], h->nvox);
+    AL(h->pb[c], h->nvox);
+  }
+  AL(h->sc, 1);
+  AL(h->red.partials, 4 * kRedBlocks);
+  AL(h->red.tickets, 8);
+  AL(h->det_err, 1);
+#undef AL
+  if (cudaMemset(h->red.tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess)
+    return cleanup(fail(h, RIHV_ERR_CUDA, "memset failed"));
+
+  // Twiddles exp(-2 pi i m / n) in FP64, rounded to float.
+  auto twiddles = [](int n) {
+    std::vector<float2> t(n);
+    for (int m = 0; m < n; ++m) {
+      const double a = -2.0 * M_PI * m / n;
+      t[m] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    }
+    return t;
+  };
+  std::vector<float2> twx = twiddles(nx), twy = twiddles(ny);
+
+  // Phase table of the angular-spectrum transfer function, strip-major
+  // [nx/W][ny][W]: phi0 = frac(z0 kappa), phid = frac(dz kappa) in units of
+  // 2^-32 cycle; amp = 1 on the propagating band.
+  std::vector<uint2> ph(h->nxy);
+  std::vector<float> am(h->nxy);
+  const double il2 = 1.0 / (wavelength * wavelength);
+  for (int ky = 0; ky < ny; ++ky) {
+    const double fy = fft_freq(ky, ny, pitch);
+    for (int kx = 0; kx < nx; ++kx) {
+      const double fx = fft_freq(kx, nx, pitch);
+      const bool prop = wavelength * wavelength * (fx * fx + fy * fy) < 1.0;
+      const double kappa = prop ? std::sqrt(il2 - fx * fx - fy * fy) : 0.0;
+      const size_t idx = (static_cast<size_t>(kx / kStrip) * ny + ky) * kStrip + (kx % kStrip);
+      ph[idx] = make_uint2(to_cycles32(frac(z0 * kappa)), to_cycles32(frac(dz * kappa)));
+      am[idx] = prop ? 1.f : 0.f;
+    }
+  }
+  if (cudaMemcpy(h->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->tw_y, twy.data(), ny * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->phase, ph.data(), h->nxy * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->amp, am.data(), h->nxy * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(fail(h, RIHV_ERR_CUDA, "upload of tables failed"));
+
+  // Step size tau = 1 / L, L = 2 max_f sum_j |H_j(f)|^2 = 2 nz on any
+  // propagating frequency (0 if none propagates).
+  bool any_prop = false;
+  for (float a : am) any_prop |= (a > 0.f);
+  h->tau = any_prop ? 1.0 / (2.0 * nz) : 0.0;
+
+  // Kernel smem limits
+  if (rows_smem_bytes(nx) > 227 * 1024 || cols_smem_bytes(COL_FWD_ZSUM, ny) > 227 * 1024)
+    return cleanup(fail(h, RIHV_ERR_UNSUPPORTED_SIZE, "shared memory limit"));
+  *out = h;
+  return RIHV_OK;
+}
+
+rihv_status rihv_destroy(rihv_handle h) {
+  if (!h) return RIHV_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->det.label) cudaFree(h->det.label);
+  if (h->det.cid) cudaFree(h->det.cid);
+  if (h->det.block_counts) cudaFree(h->det.block_counts);
+  if (h->det.maxbits) cudaFree(h->det.maxbits);
+  if (h->det.ncomp) cudaFree(h->det.ncomp);
+  if (h->det.stats) cudaFree(h->det.stats);
+  if (h->det.first) cudaFree(h->det.first);
+  if (h->trace) cudaFree(h->trace);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return RIHV_OK;
+}
+
+rihv_status rihv_set_stream(rihv_handle h, void* stream) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  h->stream = static_cast<cudaStream_t>(stream);
+  return RIHV_OK;
+}
+
+rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
+  if (!h || !o) return fail(h, RIHV_ERR_INVALID_ARG, "null argument");
+  if ((o->tv_dims != 2 && o->tv_dims != 3) || o->n_inner < 0 || o->check_every < 0 ||
+      o->tol < 0 || o->f_star < 0 || (o->restart != 0 && o->restart != 1) ||
+      (o->accelerate != 0 && o->accelerate != 1))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
+  h->opt = *o;
+  return RIHV_OK;
+}
+
+rihv_status rihv_step_size(rihv_handle h, double* tau) {
+  if (!h || !tau) return fail(h, RIHV_ERR_INVALID_ARG, "null argument");
+  *tau = h->tau;
+  return RIHV_OK;
+}
+
+rihv_status rihv_forward(rihv_handle h, const void* x, void* out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  CKS(check_dev(h, x, "x"));
+  CKS(check_dev(h, out, "out"));
+  CKS(forward_spectrum(h, static_cast<const float2*>(x), nullptr, h->spec));
+  StageScope sc(h, ST_FORWARD, 2);
+  CK(launch_cols(COL_PLAIN_INV, col_args(h, h->spec, h->inter), 1, h->stream));
+  RowArgs ra = row_args(h, h->inter, static_cast<float2*>(out), 1);
+  ra.scale = static_cast<float>(1.0 / static_cast<double>(h->nxy));
+  CK(launch_rows(1, ROW_IN_STRIP, ROW_OUT_C64, ROW_EPI_SCALE, ra, h->stream));
+  return RIHV_OK;
+}
+
+rihv_status rihv_adjoint(rihv_handle h, const void* r, void* out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  CKS(check_dev(h, r, "r"));
+  CKS(check_dev(h, out, "out"));
+  {
+    StageScope sc(h, ST_ADJOINT, 2);
+    CKS(fft2_plane(h, r, false, h->spec));
+  }
+  return adjoint_planes(h, h->spec, nullptr, static_cast<float2*>(out),
+                        static_cast<float>(1.0 / static_cast<double>(h->nxy)), false);
+}
+
+rihv_status rihv_prox_fused_lasso(rihv_handle h, const void* v, float t_l1, float t_tv,
+                                  int inner_iters, void* x_out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  CKS(check_dev(h, v, "v"));
+  CKS(check_dev(h, x_out, "x_out"));
+  if (!(t_l1 >= 0.f) || !(t_tv >= 0.f) || inner_iters < 0 || !std::isfinite(t_l1) ||
+      !std::isfinite(t_tv))
+    return fail(h, RIHV_ERR_INVALID_ARG, "t_l1, t_tv must be finite and >= 0, inner_iters >= 0");
+  if (v == x_out) return fail(h, RIHV_ERR_INVALID_ARG, "v and x_out must not alias");
+  return prox_into(h, static_cast<const float2*>(v), t_l1, t_tv, inner_iters, FIN_PROX,
+                   static_cast<float2*>(x_out));
+}
+
+rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, float lambda_tv,
+                       int iters, const void* x0, void* x_out, double* trace, int* iters_done) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (!hologram || !x_out) return fail(h, RIHV_ERR_INVALID_ARG, "hologram and x_out are required");
+  if (iters < 0 || !(lambda_l1 >= 0.f) || !(lambda_tv >= 0.f) || !std::isfinite(lambda_l1) ||
+      !std::isfinite(lambda_tv))
+    return fail(h, RIHV_ERR_INVALID_ARG, "iters >= 0 and finite lambdas >= 0 required");
+  if (is_device_ptr(x_out) && !aligned16(x_out))
+    return fail(h, RIHV_ERR_INVALID_ARG, "x_out is not 16-byte aligned");
+  const size_t vb = h->nvox * sizeof(float2);
+  const int M = h->opt.check_every;
+  const int nchecks = (M > 0) ? iters / M : 0;
+  if (nchecks > h->trace_cap) {
+    if (h->trace) cudaFree(h->trace);
+    h->trace = nullptr;
+    h->trace_cap = 0;
+    if (cudaMalloc(&h->trace, sizeof(double) * nchecks) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RIHV_ERR_OOM, "trace allocation failed");
+    }
+    h->trace_cap = nchecks;
+  }
+  const bool stop_test = h->opt.f_star > 0.0 && M > 0;
+
+  // Hologram and its spectrum F b.
+  CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
+  CKS(fft2_plane(h, h->holo, true, h->bhat));
+  // x_0 and y_1 = x_0
+  if (x0)
+    CKS(copy_in(h, h->x, x0, vb));
+  else
+    CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
+  CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
+
+  const float tau = static_cast<float>(h->tau);
+  const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
+  int done = 0;
+  int check = 0;
+  for (int k = 1; k <= iters; ++k) {
+    // (a) forward and residual spectrum R = F(H y - b)
+    CKS(forward_spectrum(h, h->y, h->bhat, h->spec));
+    // (c) v = y - tau * 2 H^H r
+    CKS(adjoint_planes(h, h->spec, h->y, h->v, grad_scale, true));
+    // (d) x_k = prox(v), momentum, restart
+    CKS(prox_into(h, h->v, tau * lambda_l1, tau * lambda_tv, h->opt.n_inner, FIN_FISTA, h->x));
+    done = k;
+    if (M > 0 && k % M == 0) {
+      CKS(forward_spectrum(h, h->x, h->bhat, h->spec));
+      {
+        StageScope sc(h, ST_OBJECTIVE, 1);
+        CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, lambda_l1, lambda_tv, h->sc,
+                            h->red, h->trace + check, h->stream));
+      }
+      if (stop_test) {
+        double f = 0;
+        CK(cudaMemcpyAsync(&f, h->trace + check, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        ++check;
+        if (f <= h->opt.f_star * (1.0 + h->opt.tol)) break;
+      } else {
+        ++check;
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(x_out, h->x, vb, cudaMemcpyDefault, h->stream));
+  if (trace && check > 0)
+    CK(cudaMemcpyAsync(trace, h->trace, sizeof(double) * check, cudaMemcpyDefault, h->stream));
+  DevScalars hs{};
+  CK(cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (iters_done) *iters_done = done;
+  if (hs.nonfinite) return fail(h, RIHV_ERR_NONFINITE, "a reduction produced NaN or Inf");
+  return RIHV_OK;
+}
+
+rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
+                        rihv_particle* out, int max_out, int* n_out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  CKS(check_dev(h, x, "x"));
+  if (!n_out || (max_out > 0 && !out) || max_out < 0 || min_vox < 0 || !(rel_thresh >= 0.f) ||
+      !std::isfinite(rel_thresh))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid detect arguments");
+  if (h->nvox >= static_cast<size_t>(INT32_MAX))
+    return fail(h, RIHV_ERR_UNSUPPORTED_SIZE, "volume too large for int32 labels");
+  DetectWork& w = h->det;
+  const size_t nb = (h->nvox + 1023) / 1024;
+  if (!w.label) {
+    if (cudaMalloc(&w.label, h->nvox * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&w.cid, h->nvox * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&w.block_counts, nb * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&w.maxbits, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&w.ncomp, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RIHV_ERR_OOM, "detection scratch allocation failed");
+    }
+  }
+  StageScope scope(h, ST_DETECT, 9);
+  int ncomp = 0;
+  CK(detect_label(static_cast<const float2*>(x), h->nx, h->ny, h->nz, rel_thresh, w, h->det_err,
+                  &ncomp, h->stream));
+  if (static_cast<size_t>(ncomp) > w.capacity) {
+    if (w.stats) cudaFree(w.stats);
+    if (w.first) cudaFree(w.first);
+    w.stats = nullptr;
+    w.first = nullptr;
+    w.capacity = 0;
+    const size_t cap = std::max<size_t>(ncomp, 1024);
+    if (cudaMalloc(&w.stats, cap * 5 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&w.first, cap * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RIHV_ERR_OOM, "detection stats allocation failed");
+    }
+    w.capacity = cap;
+  }
+  std::vector<double> st(static_cast<size_t>(ncomp) * 5);
+  std::vector<long long> first(ncomp);
+  int err = 0;
+  if (ncomp > 0) {
+    CK(detect_stats(static_cast<const float2*>(x), h->nx, h->ny, h->nz, w, ncomp, h->stream));
+    CK(cudaMemcpyAsync(st.data(), w.stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(first.data(), w.first, first.size() * sizeof(long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaMemcpyAsync(&err, h->det_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err) return fail(h, RIHV_ERR_TIMEOUT, "union-find exceeded its iteration bound");
+  int n = 0;
+  for (int c = 0; c < ncomp; ++c) {
+    const double* s = &st[static_cast<size_t>(c) * 5];
+    const int cnt = static_cast<int>(s[4] + 0.5);
+    if (cnt <= min_vox) continue;
+    if (n < max_out) {
+      rihv_particle& p = out[n];
+      p.cx = s[1] / s[0];
+      p.cy = s[2] / s[0];
+      p.cz = s[3] / s[0];
+      p.weight = s[0];
+      p.first = first[c];
+      p.nvox = cnt;
+      p.pad_ = 0;
+    }
+    ++n;
+  }
+  *n_out = n;
+  return RIHV_OK;
+}
+
+rihv_status rihv_set_profiling(rihv_handle h, int on) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (on && h->ev_pool.empty()) {
+    h->ev_pool.resize(kEventPool);
+    for (auto& e : h->ev_pool) CK(cudaEventCreate(&e));
+  }
+  h->prof = on != 0;
+  return RIHV_OK;
+}
+
+rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int n) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    h->stage_ms[r.stage] += t;
+    h->stage_launches[r.stage] += r.launches;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+  for (int i = 0; i < kNumStages && i < n; ++i) {
+    if (ms) ms[i] = h->stage_ms[i];
+    if (launches) launches[i] = h->stage_launches[i];
+    h->stage_ms[i] = 0;
+    h->stage_launches[i] = 0;
+  }
+  return RIHV_OK;
+}
+
+}  // extern "C"

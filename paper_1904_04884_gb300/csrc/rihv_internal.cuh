@@ -1,0 +1,156 @@
+// Internal declarations shared by the librihv translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rihv.h"
+
+namespace rihv {
+
+// ---------------------------------------------------------------------------
+// Sizes and launch shapes
+// ---------------------------------------------------------------------------
+constexpr int kMaxN = 1024;        // largest supported nx, ny
+constexpr int kRowsPerCta = 4;     // transforms per CTA in the row pass
+constexpr int kStrip = 4;          // strip width of the intermediate layout
+constexpr int kFftThreads = 512;   // threads per FFT CTA
+constexpr int kMaxPasses = 8;
+
+constexpr int kTvTx = 32;          // TV tile width (x)
+constexpr int kTvTy = 8;           // TV tile height (y)
+constexpr int kTvThreads = kTvTx * kTvTy;
+
+constexpr int kRedBlocks = 1216;   // fixed grid of the streaming reduction kernels (8 x 152)
+constexpr int kRedThreads = 256;
+
+// Radix plan of one 1D transform of length n = product of radix[0..npass).
+struct FftPlan {
+  int n;
+  int npass;
+  int radix[kMaxPasses];
+};
+
+// Scalars that live on the device between kernels of one solve.
+struct DevScalars {
+  double t;            // FISTA t_k
+  double beta;         // momentum factor of the current iteration
+  double restart_dot;  // Re<y_k - x_k, x_k - x_{k-1}> of the last iteration
+  double rnorm2;       // ||H x - b||^2 of the last forward with a hologram
+  double l1;           // ||x||_1 of the last objective evaluation
+  double tv;           // TV(x) of the last objective evaluation
+  int restart_flag;    // 1 if the last finalize restarted the momentum
+  int nonfinite;       // sticky: a reduction saw NaN/Inf
+  int accelerate;      // FISTA momentum on
+  int restart;         // gradient restart enabled
+};
+
+// Reduction workspace: per-block partials and last-block tickets.
+struct RedWork {
+  double* partials;    // [4][kRedBlocks]
+  unsigned* tickets;   // [8]
+};
+
+// ---------------------------------------------------------------------------
+// FFT pass kernels (fft_kernels.cu)
+// ---------------------------------------------------------------------------
+enum RowIn { ROW_IN_C64 = 0, ROW_IN_F32 = 1, ROW_IN_STRIP = 2 };
+enum RowOut { ROW_OUT_C64 = 0, ROW_OUT_STRIP = 1 };
+enum RowEpi { ROW_EPI_SCALE = 0, ROW_EPI_GRAD = 1 };
+
+struct RowArgs {
+  const void* src;     // input planes (layout per RowIn)
+  float2* dst;         // output planes (layout per RowOut)
+  const float2* y;     // ROW_EPI_GRAD: volume y, row-major
+  int nx, ny, nz;
+  float scale;         // ROW_EPI_SCALE: out = scale * g; ROW_EPI_GRAD: v = y - scale * g
+  FftPlan plan;        // along x
+  const float2* tw;    // twiddles exp(-2 pi i m / nx), m < nx
+};
+
+enum ColMode { COL_FWD_ZSUM = 0, COL_ADJ_GEN = 1, COL_PLAIN_FWD = 2, COL_PLAIN_INV = 3 };
+
+struct ColArgs {
+  const float2* src;
+  float2* dst;
+  const uint2* phase;  // [ny][nx] {phi0, phid}: plane j has phase phi0 + j*phid (2^-32 cycles)
+  const float* amp;    // [ny][nx] 1 on the propagating band, 0 otherwise
+  int nx, ny, nz;
+  int z_per_group;     // planes per CTA along blockIdx.y
+  float scale;
+  FftPlan plan;        // along y
+  const float2* tw;    // twiddles exp(-2 pi i m / ny), m < ny
+};
+
+cudaError_t launch_rows(int dir_inverse, int in, int out, int epi, const RowArgs& a,
+                        cudaStream_t s);
+cudaError_t launch_cols(int mode, const ColArgs& a, int groups, cudaStream_t s);
+size_t rows_smem_bytes(int nx);
+size_t cols_smem_bytes(int mode, int ny);
+
+// S = sum_g partial[g]; if bhat: out = S - bhat and ||out||^2 / (nx ny) -> sc->rnorm2.
+cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, float2* out,
+                        int nx, int ny, DevScalars* sc, RedWork w, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// TV / prox / FISTA kernels (tv_kernels.cu)
+// ---------------------------------------------------------------------------
+struct TvArgs {
+  const float2* v;
+  const float2* pin[3];
+  float2* pout[3];
+  int nx, ny, nz, dims;
+  int zchunk;
+  float mu;            // t_tv
+  float step;          // 1 / (4 dims mu)
+};
+cudaError_t launch_tv_step(bool first, const TvArgs& a, cudaStream_t s);
+
+enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };
+struct FinArgs {
+  const float2* v;
+  const float2* p[3];  // may be null (no TV): u = v
+  const float2* x_prev;
+  const float2* y;
+  float2* x_out;
+  float2* y_out;
+  int nx, ny, nz, dims;
+  float mu;            // t_tv
+  float kappa;         // t_l1
+  DevScalars* sc;
+  RedWork w;
+};
+cudaError_t launch_finalize(int mode, const FinArgs& a, cudaStream_t s);
+cudaError_t launch_restart_fixup(const float2* x, float2* y, size_t nvox, const DevScalars* sc,
+                                 cudaStream_t s);
+// F = sc->rnorm2 + lam_l1 * L1(x) + lam_tv * TV(x) -> *f_out (device double)
+cudaError_t launch_objective(const float2* x, int nx, int ny, int nz, int dims, double lam_l1,
+                             double lam_tv, DevScalars* sc, RedWork w, double* f_out,
+                             cudaStream_t s);
+cudaError_t launch_init_scalars(DevScalars* sc, int accelerate, int restart, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Detection (detect_kernels.cu)
+// ---------------------------------------------------------------------------
+struct DetectWork {
+  int* label = nullptr;          // [nvox] union-find parent, -1 below threshold
+  int* cid = nullptr;            // [nvox] compact component id, valid at roots
+  unsigned* block_counts = nullptr;  // [nblocks] roots per 1024 voxels, then offsets
+  unsigned* maxbits = nullptr;   // [1] max |x|^2 as float bits
+  int* ncomp = nullptr;          // [1]
+  double* stats = nullptr;       // [capacity][5]: sum w, sum w*i, sum w*j, sum w*k, count
+  long long* first = nullptr;    // [capacity] smallest linear index
+  size_t capacity = 0;
+};
+// Threshold, label, flatten, count roots; *ncomp_host receives the number of
+// components (synchronises the stream). *err_dev is set if a union-find loop
+// hit its bound.
+cudaError_t detect_label(const float2* x, int nx, int ny, int nz, float rel, DetectWork& w,
+                         int* err_dev, int* ncomp_host, cudaStream_t s);
+// Component ids, first indices and FP64 sums for ncomp <= w.capacity components.
+cudaError_t detect_stats(const float2* x, int nx, int ny, int nz, DetectWork& w, int ncomp,
+                         cudaStream_t s);
+
+}  // namespace rihv

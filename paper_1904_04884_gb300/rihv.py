@@ -1,0 +1,230 @@
+"""Python binding of librihv (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts tensors and
+arrays to raw pointers, checks shapes and dtypes, and raises ``RihvError`` on a
+non-zero status. Importing works without a GPU; the first call that needs the
+library raises if ``lib/librihv.so`` has not been built.
+
+Accepted buffers: torch tensors (CUDA for device arguments, CPU for host
+arguments), numpy arrays (host), or raw integer addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "librihv.so")
+
+STATUS = {0: "RIHV_OK", 1: "RIHV_ERR_INVALID_ARG", 2: "RIHV_ERR_CUDA", 3: "RIHV_ERR_OOM",
+          4: "RIHV_ERR_NONFINITE", 5: "RIHV_ERR_TIMEOUT", 6: "RIHV_ERR_UNSUPPORTED_SIZE"}
+
+EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stream",
+           "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
+           "rihv_solve", "rihv_detect", "rihv_set_profiling", "rihv_stage_times",
+           "rihv_step_size", "rihv_last_error"]
+
+STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect"]
+
+
+class RihvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tv_dims", ctypes.c_int), ("restart", ctypes.c_int),
+                ("accelerate", ctypes.c_int), ("n_inner", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
+                ("f_star", ctypes.c_double)]
+
+
+class Particle(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+                ("weight", ctypes.c_double), ("first", ctypes.c_int64), ("nvox", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads librihv.so and declares its signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librihv.so not found at {path}; build it with "
+                           "`python -m paper_1904_04884_gb300.build`")
+    L = ctypes.CDLL(path)
+    vp, i, d, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float
+    H = ctypes.c_void_p
+    sig = {
+        "rihv_default_options": (None, [ctypes.POINTER(Options)]),
+        "rihv_create": (i, [i, i, i, d, d, d, d, ctypes.POINTER(H)]),
+        "rihv_destroy": (i, [H]),
+        "rihv_set_stream": (i, [H, vp]),
+        "rihv_set_options": (i, [H, ctypes.POINTER(Options)]),
+        "rihv_forward": (i, [H, vp, vp]),
+        "rihv_adjoint": (i, [H, vp, vp]),
+        "rihv_prox_fused_lasso": (i, [H, vp, f, f, i, vp]),
+        "rihv_solve": (i, [H, vp, f, f, i, vp, vp, vp, ctypes.POINTER(i)]),
+        "rihv_detect": (i, [H, vp, f, i, ctypes.POINTER(Particle), i, ctypes.POINTER(i)]),
+        "rihv_set_profiling": (i, [H, i]),
+        "rihv_stage_times": (i, [H, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
+        "rihv_step_size": (i, [H, ctypes.POINTER(d)]),
+        "rihv_last_error": (ctypes.c_char_p, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(buf, *, device=None, dtype=None, numel=None, name="buffer"):
+    """Raw address of a torch tensor, numpy array or int (None -> 0)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        if device is True:
+            raise ValueError(f"{name} must be device memory")
+        if not buf.flags.c_contiguous:
+            raise ValueError(f"{name} must be C-contiguous")
+        if dtype is not None and buf.dtype != np.dtype(dtype):
+            raise ValueError(f"{name} must be {np.dtype(dtype)}, got {buf.dtype}")
+        if numel is not None and buf.size != numel:
+            raise ValueError(f"{name} has {buf.size} elements, expected {numel}")
+        return buf.ctypes.data
+    # torch tensor
+    if not buf.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is True and not buf.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None:
+        want = {"complex64": "torch.complex64", "float32": "torch.float32",
+                "float64": "torch.float64"}[np.dtype(dtype).name]
+        if str(buf.dtype) != want:
+            raise ValueError(f"{name} must be {want}, got {buf.dtype}")
+    if numel is not None and buf.numel() != numel:
+        raise ValueError(f"{name} has {buf.numel()} elements, expected {numel}")
+    return buf.data_ptr()
+
+
+class Rihv:
+    """One reconstruction grid and optics (a ``rihv_handle``)."""
+
+    def __init__(self, nx, ny, nz, wavelength, pitch, z0, dz, stream=None):
+        self.L = load_library()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.nxy = self.nx * self.ny
+        self.nvox = self.nxy * self.nz
+        h = ctypes.c_void_p()
+        self._check(self.L.rihv_create(self.nx, self.ny, self.nz, float(wavelength), float(pitch),
+                                       float(z0), float(dz), ctypes.byref(h)), None)
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, st, h):
+        if st != 0:
+            msg = self.L.rihv_last_error(h)
+            raise RihvError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rihv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self._check(self.L.rihv_set_stream(self.h, ptr), self.h)
+
+    def set_options(self, **kw):
+        o = Options()
+        self.L.rihv_default_options(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        self._check(self.L.rihv_set_options(self.h, ctypes.byref(o)), self.h)
+        self.options = o
+
+    def step_size(self) -> float:
+        t = ctypes.c_double()
+        self._check(self.L.rihv_step_size(self.h, ctypes.byref(t)), self.h)
+        return t.value
+
+    # -- operators ----------------------------------------------------------
+    def rihv_forward(self, x, out):
+        self._check(self.L.rihv_forward(
+            self.h, _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x"),
+            _ptr(out, device=True, dtype="complex64", numel=self.nxy, name="out")), self.h)
+
+    def rihv_adjoint(self, r, out):
+        self._check(self.L.rihv_adjoint(
+            self.h, _ptr(r, device=True, dtype="complex64", numel=self.nxy, name="r"),
+            _ptr(out, device=True, dtype="complex64", numel=self.nvox, name="out")), self.h)
+
+    def rihv_prox_fused_lasso(self, v, t_l1, t_tv, inner_iters, x_out):
+        self._check(self.L.rihv_prox_fused_lasso(
+            self.h, _ptr(v, device=True, dtype="complex64", numel=self.nvox, name="v"),
+            float(t_l1), float(t_tv), int(inner_iters),
+            _ptr(x_out, device=True, dtype="complex64", numel=self.nvox, name="x_out")), self.h)
+
+    def rihv_solve(self, hologram, lambda_l1, lambda_tv, iters, x_out, x0=None, trace=None):
+        """Runs FISTA; returns the number of iterations run."""
+        done = ctypes.c_int()
+        self._check(self.L.rihv_solve(
+            self.h, _ptr(hologram, dtype="float32", numel=self.nxy, name="hologram"),
+            float(lambda_l1), float(lambda_tv), int(iters),
+            _ptr(x0, dtype="complex64", numel=self.nvox, name="x0"),
+            _ptr(x_out, dtype="complex64", numel=self.nvox, name="x_out"),
+            _ptr(trace, dtype="float64", name="trace"), ctypes.byref(done)), self.h)
+        return done.value
+
+    def rihv_detect(self, x, rel_thresh=2.0 / 256.0, min_vox=5, max_out=1 << 20):
+        """Returns a list of particle dicts ordered by smallest voxel index."""
+        n = ctypes.c_int()
+        arr = (Particle * max(1, max_out))()
+        self._check(self.L.rihv_detect(
+            self.h, _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x"),
+            float(rel_thresh), int(min_vox), arr, int(max_out), ctypes.byref(n)), self.h)
+        out = []
+        for k in range(min(n.value, max_out)):
+            p = arr[k]
+            out.append(dict(centroid=(p.cx, p.cy, p.cz), nvox=p.nvox, weight=p.weight,
+                            first=p.first))
+        return out
+
+    # -- profiling ----------------------------------------------------------
+    def set_profiling(self, on: bool):
+        self._check(self.L.rihv_set_profiling(self.h, 1 if on else 0), self.h)
+
+    def stage_times(self):
+        """{stage: (ms, launches)} accumulated since the last call."""
+        ms = (ctypes.c_double * 6)()
+        nl = (ctypes.c_longlong * 6)()
+        self._check(self.L.rihv_stage_times(self.h, ms, nl, 6), self.h)
+        return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
+
+    # short aliases
+    forward = rihv_forward
+    adjoint = rihv_adjoint
+    prox_fused_lasso = rihv_prox_fused_lasso
+    solve = rihv_solve
+    detect = rihv_detect
