@@ -1,0 +1,333 @@
+"""Benchmark of the fused-lasso FISTA reconstruction on one GB300 per rank.
+
+One step = one complete reconstruction of the 512 x 512 x 128 particle-field
+hologram (200 FISTA iterations, 20 TV dual steps per prox, objective every 10
+iterations, then particle detection), all through the C ABI.
+
+value  : voxel-iterations/s with hologram and volumes resident in HBM.
+e2e    : the same metric with pinned HOST buffers: the hologram is copied in
+         and the volume copied out inside rihv_solve, every step.
+roofline: the TV dual-step kernel (the dominant kernel), from CUDA events the
+         library records around its stages on its own stream during the timed
+         steps; algorithmic bytes 32 (first step) + 56 per later step per voxel.
+cpu_baseline: the FP64 oracle on a bounded sample (two FISTA iterations on a
+         16-plane slab of the same workload), host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank reconstructs its own hologram (independent work, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TV_PROFILE = os.path.join(ROOT, "profiles", "tv_step_traffic.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx = float(parts[2].split()[0])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        med = float(np.median(sm)) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_1904_04884_gb300", "csrc", "tv_kernels.cu"), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1904_04884_gb300", "csrc", "rihv_internal.cuh"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(nvox):
+    """DRAM bytes per TV-step launch from the committed ncu summary, scaled to
+    this workload, or None when the kernel changed since it was captured."""
+    try:
+        prof = json.load(open(TV_PROFILE))
+    except Exception:
+        return None
+    if prof.get("kernel_hash") != kernel_hash():
+        return None
+    return prof["dram_bytes_per_voxel_per_launch"] * nvox
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(PEAKS))["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_hologram(w, h, torch, dev):
+    """Opacity volume from the seeded generator; hologram via this library's
+    forward operator: b = 1 - |1 - H a|^2 + sigma n."""
+    from paper_1904_04884_gb300 import synth
+    a = torch.from_numpy(w.opacity().astype(np.complex64)).to(dev)
+    field = torch.empty((w.ny, w.nx), dtype=torch.complex64, device=dev)
+    h.forward(a, field)
+    torch.cuda.synchronize()
+    b = synth.intensity_hologram(field.cpu().numpy().astype(np.complex128), w.sigma, w.noise())
+    del a
+    return b
+
+
+def cpu_baseline_sample(w, iters=2, planes=16):
+    """The FP64 oracle, as it stands, on a slab of the workload: `planes`
+    planes of the same optics, `iters` FISTA iterations. Returns voxel-iter/s."""
+    from oracle import rihv_oracle as O
+    from paper_1904_04884_gb300 import synth
+    op = O.Optics(w.nx, w.ny, planes, w.wavelength, w.pitch, w.z0, w.dz)
+    a = w.opacity()[:planes].astype(np.float64)
+    b = synth.intensity_hologram(O.forward(a, op), w.sigma, w.noise())
+    t0 = time.perf_counter()
+    O.fista(b.astype(np.float64), op, w.lam_l1, w.lam_tv, iters, w.n_inner)
+    dt = time.perf_counter() - t0
+    return w.nx * w.ny * planes * iters / dt, dt
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample (one FISTA iteration on a 16-plane slab) of the same workload."""
+    if rank != 0:
+        return
+    from paper_1904_04884_gb300 import workloads
+    from oracle import rihv_oracle as O
+    from paper_1904_04884_gb300 import synth
+    w = workloads.MID
+    planes = 16
+    op = O.Optics(w.nx, w.ny, planes, w.wavelength, w.pitch, w.z0, w.dz)
+    a = w.opacity()[:planes].astype(np.float64)
+    b = synth.intensity_hologram(O.forward(a, op), w.sigma, w.noise()).astype(np.float64)
+    for _ in range(args.warmup):
+        O.fista(b, op, w.lam_l1, w.lam_tv, 1, w.n_inner)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.fista(b, op, w.lam_l1, w.lam_tv, 1, w.n_inner)
+    dt = time.perf_counter() - t0
+    value = w.nx * w.ny * planes * args.steps / dt
+    sample = f"1 FISTA iteration (K={w.n_inner}) on a {w.nx}x{w.ny}x{planes} slab per step"
+    line = {
+        "impl": "reference", "metric": "voxel-iterations/s", "value": value,
+        "unit": "voxel-iter/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if pg:
+            pg.barrier()
+        return
+
+    import torch
+    from paper_1904_04884_gb300 import workloads
+    from paper_1904_04884_gb300.rihv import Rihv
+
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.MID
+    stream = torch.cuda.Stream(device=dev)
+    h = Rihv(*w.optics_tuple(), stream=stream)
+    h.set_options(tv_dims=w.tv_dims, n_inner=w.n_inner, check_every=10)
+
+    b = make_hologram(w, h, torch, dev)
+    # each rank reconstructs its own frame: a different noise draw per rank
+    if rank:
+        from paper_1904_04884_gb300 import synth
+        b = (b + w.sigma * synth.Stream(1000 + rank).normal(w.nx * w.ny).reshape(b.shape)
+             ).astype(np.float32)
+    b_dev = torch.from_numpy(b).to(dev)
+    x_dev = torch.empty(w.shape, dtype=torch.complex64, device=dev)
+    trace = torch.empty(w.iters // 10, dtype=torch.float64, device=dev)
+
+    def step_device():
+        h.solve(b_dev, w.lam_l1, w.lam_tv, w.iters, x_dev, trace=trace)
+        return h.detect(x_dev, 2.0 / 256.0, 5)
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    h.stage_times()                      # reset counters
+    h.set_profiling(True)
+
+    sampler = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ndet = 0
+    for _ in range(args.steps):
+        ndet = len(step_device())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    stages = h.stage_times()
+    h.set_profiling(False)
+
+    # End to end through the public call with pinned host buffers.
+    b_host = torch.from_numpy(b).pin_memory()
+    x_host = torch.empty(w.shape, dtype=torch.complex64).pin_memory()
+    trace_host = np.zeros(w.iters // 10)
+
+    def step_host():
+        h.solve(b_host, w.lam_l1, w.lam_tv, w.iters, x_host, trace=trace_host)
+        return h.detect(None, 2.0 / 256.0, 5)     # detection on the solve's own result
+
+    step_host()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        step_host()
+    e2e_s = time.perf_counter() - t0
+
+    times = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64)
+    if pg:
+        pg.all_reduce(times, op=pg.ReduceOp.MAX)
+    ms, e2e_ms = float(times[0]), float(times[1])
+
+    if rank != 0:
+        return
+    vox_iters = w.nvox * w.iters
+    value = vox_iters * args.steps * world / (ms / 1e3)
+    e2e_value = vox_iters * e2e_steps * world / (e2e_ms / 1e3)
+
+    # roofline of the TV dual step, from the live stage events
+    tv_ms, tv_launches = stages["tv"]
+    per_prox = w.n_inner
+    alg_bytes_per_launch = w.nvox * (32 + 56 * (per_prox - 1)) / per_prox
+    avg_launch_s = (tv_ms / 1e3) / max(tv_launches, 1)
+    achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if tv_launches else None
+    peak, peak_kind = hbm_peak()
+    total_launches = sum(n for _, n in stages.values())
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt = cpu_baseline_sample(w)
+        cpu = {"value": v, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"2 FISTA iterations (K={w.n_inner}) on a {w.nx}x{w.ny}x16 slab "
+                         f"of the same workload, {dt:.1f} s, numpy FP64 single thread"}
+
+    line = {
+        "metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (f32 complex, f64 reductions)", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "iters": w.iters,
+                   "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
+                   "step": "full FISTA solve + objective every 10 iters + detection",
+                   "l2": "inputs larger than L2 (268 MB per volume)",
+                   "detections": ndet, "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "voxel-iter/s",
+                "h2d_bytes_per_step": int(w.nx * w.ny * 4),
+                "d2h_bytes_per_step": int(w.nvox * 8 + (w.iters // 10) * 8)},
+        "gpu_launches": int(total_launches),
+        "roofline": {"bound": "hbm", "kernel": "k_tv_step", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": measured_traffic(w.nvox), "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes_per_launch,
+                     "avg_launch_ms": avg_launch_s * 1e3},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

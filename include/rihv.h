@@ -26,8 +26,9 @@
  *  - All work is queued on the handle's stream (rihv_set_stream; default: the
  *    legacy default stream). Calls return once the work is queued unless they
  *    say otherwise. The caller owns every pointer it passes; the library owns
- *    its scratch, which rihv_create allocates and rihv_destroy frees. No call
- *    other than rihv_create and rihv_detect (first use) allocates memory.
+ *    its scratch, which rihv_create allocates and rihv_destroy frees. Only
+ *    rihv_create, rihv_detect (labelling scratch) and rihv_solve (a larger
+ *    objective trace than before) allocate; the iteration itself never does.
  *  - Errors: every call returns a status; arguments are checked before any
  *    launch. rihv_last_error() gives a message for the last failing call on
  *    the handle. A handle is not thread safe.
@@ -123,9 +124,9 @@ rihv_status rihv_prox_fused_lasso(rihv_handle h, const void* v, float t_l1, floa
  * objective_trace_or_null: host or device double array with one slot per
  *   objective check (iters / check_every entries), or NULL.
  * If *iters_done is non-NULL it receives the iterations actually run (fewer
- * than iters only when the f_star stop test fired). With host output
- * pointers or an active stop test the call returns after the stream
- * finishes; otherwise it returns once the work is queued. */
+ * than iters only when the f_star stop test fired). The call returns after
+ * the stream has finished the solve; a non-finite objective or norm returns
+ * RIHV_ERR_NONFINITE. */
 rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, float lambda_tv,
                        int iters, const void* x0_or_null, void* x_out,
                        double* objective_trace_or_null, int* iters_done);
@@ -135,17 +136,22 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
  * of <= min_vox voxels dropped, |x|-weighted centroids. Particles are written
  * to host array `out` (capacity max_out) in order of their smallest linear
  * voxel index; *n_out receives the number found (which may exceed max_out;
- * only max_out are written). x: device complex64 [nz][ny][nx]. Synchronises
- * the stream. The first call allocates the labelling scratch. */
+ * only max_out are written). x: device complex64 [nz][ny][nx], or NULL for
+ * the result of the last rihv_solve on this handle (which the library keeps
+ * on the device even when x_out was host memory). Synchronises
+ * the stream. The first call allocates the labelling scratch, and a call that
+ * finds more components than any before grows the per-component buffers. */
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
                         rihv_particle* out, int max_out, int* n_out);
 
-/* Per-stage timing. When on, the library records CUDA events around its
- * stages on the handle's stream; rihv_stage_times then returns accumulated
- * milliseconds and launch counts per stage (after synchronising the stream)
- * and resets them. Stages, in order: 0 forward, 1 adjoint+gradient step,
- * 2 TV dual steps, 3 finalize (soft threshold, momentum, restart), 4 objective,
- * 5 detection. n is the capacity of both arrays (up to 6 are written). */
+/* Per-stage timing. Kernel launches are always counted per stage. When
+ * profiling is on, the library also records CUDA events around its stages on
+ * the handle's stream. rihv_stage_times returns accumulated milliseconds (0
+ * without profiling) and launch counts per stage, after synchronising the
+ * stream, and resets both. Stages, in order: 0 forward, 1 adjoint + gradient
+ * step, 2 TV dual steps, 3 finalize (soft threshold, momentum, restart),
+ * 4 objective, 5 detection, 6 solve set-up (hologram spectrum, x_0, scalars).
+ * n is the capacity of both arrays (up to 7 are written); either may be NULL. */
 rihv_status rihv_set_profiling(rihv_handle h, int on);
 rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int n);
 

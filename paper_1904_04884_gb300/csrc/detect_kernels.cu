@@ -21,7 +21,7 @@ namespace rihv {
 namespace {
 
 constexpr int kDetThreads = 1024;
-constexpr int kUfLimit = 1 << 24;   // bound on union/find retries (never reached in practice)
+constexpr int kUfLimit = 1 << 20;   // bound on union/find retries (never reached in practice)
 
 __device__ __forceinline__ float mag2_rn(float2 c) {
   return __fadd_rn(__fmul_rn(c.x, c.x), __fmul_rn(c.y, c.y));

@@ -20,8 +20,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
-constexpr int kNumStages = 6;
-enum Stage { ST_FORWARD = 0, ST_ADJOINT = 1, ST_TV = 2, ST_FINAL = 3, ST_OBJECTIVE = 4, ST_DETECT = 5 };
+constexpr int kNumStages = 7;
+enum Stage {
+  ST_FORWARD = 0, ST_ADJOINT = 1, ST_TV = 2, ST_FINAL = 3, ST_OBJECTIVE = 4, ST_DETECT = 5,
+  ST_SETUP = 6
+};
 constexpr int kEventPool = 8192;
 
 bool supported_n(int n) {
@@ -170,6 +173,7 @@ struct StageScope {
   int launches;
   cudaEvent_t a = nullptr;
   StageScope(rihv_ctx* hh, int st, int nl) : h(hh), stage(st), launches(nl) {
+    h->stage_launches[stage] += launches;
     if (!h->prof) return;
     if (h->ev_used + 2 > h->ev_pool.size()) flush();
     a = h->ev_pool[h->ev_used++];
@@ -179,7 +183,7 @@ struct StageScope {
     if (!h->prof || !a) return;
     cudaEvent_t b = h->ev_pool[h->ev_used++];
     cudaEventRecord(b, h->stream);
-    h->recs.push_back({stage, launches, a, b});
+    h->recs.push_back({stage, 0, a, b});
   }
   void flush() {
     cudaStreamSynchronize(h->stream);
@@ -187,7 +191,6 @@ struct StageScope {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, r.a, r.b);
       h->stage_ms[r.stage] += ms;
-      h->stage_launches[r.stage] += r.launches;
     }
     h->recs.clear();
     h->ev_used = 0;
@@ -547,16 +550,18 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
   }
   const bool stop_test = h->opt.f_star > 0.0 && M > 0;
 
-  // Hologram and its spectrum F b.
-  CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
-  CKS(fft2_plane(h, h->holo, true, h->bhat));
-  // x_0 and y_1 = x_0
-  if (x0)
-    CKS(copy_in(h, h->x, x0, vb));
-  else
-    CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
-  CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
-  CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
+  {
+    // Hologram and its spectrum F b; x_0 and y_1 = x_0; scalars.
+    StageScope sc(h, ST_SETUP, 3);
+    CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
+    CKS(fft2_plane(h, h->holo, true, h->bhat));
+    if (x0)
+      CKS(copy_in(h, h->x, x0, vb));
+    else
+      CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
+    CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
+  }
 
   const float tau = static_cast<float>(h->tau);
   const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
@@ -602,6 +607,7 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
                         rihv_particle* out, int max_out, int* n_out) {
   if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (!x) x = h->x;   // the last solve's result
   CKS(check_dev(h, x, "x"));
   if (!n_out || (max_out > 0 && !out) || max_out < 0 || min_vox < 0 || !(rel_thresh >= 0.f) ||
       !std::isfinite(rel_thresh))
@@ -620,7 +626,7 @@ rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_
       return fail(h, RIHV_ERR_OOM, "detection scratch allocation failed");
     }
   }
-  StageScope scope(h, ST_DETECT, 9);
+  StageScope scope(h, ST_DETECT, 8);
   int ncomp = 0;
   CK(detect_label(static_cast<const float2*>(x), h->nx, h->ny, h->nz, rel_thresh, w, h->det_err,
                   &ncomp, h->stream));
@@ -689,7 +695,6 @@ rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, r.a, r.b));
     h->stage_ms[r.stage] += t;
-    h->stage_launches[r.stage] += r.launches;
   }
   h->recs.clear();
   h->ev_used = 0;

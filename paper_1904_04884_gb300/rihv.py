@@ -26,7 +26,7 @@ EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stre
            "rihv_solve", "rihv_detect", "rihv_set_profiling", "rihv_stage_times",
            "rihv_step_size", "rihv_last_error"]
 
-STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect"]
+STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup"]
 
 
 class RihvError(RuntimeError):
@@ -198,11 +198,12 @@ class Rihv:
         return done.value
 
     def rihv_detect(self, x, rel_thresh=2.0 / 256.0, min_vox=5, max_out=1 << 20):
-        """Returns a list of particle dicts ordered by smallest voxel index."""
+        """Returns a list of particle dicts ordered by smallest voxel index.
+        x = None detects on the result of the last solve on this handle."""
         n = ctypes.c_int()
         arr = (Particle * max(1, max_out))()
         self._check(self.L.rihv_detect(
-            self.h, _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x"),
+            self.h, _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x") or None,
             float(rel_thresh), int(min_vox), arr, int(max_out), ctypes.byref(n)), self.h)
         out = []
         for k in range(min(n.value, max_out)):
@@ -217,9 +218,9 @@ class Rihv:
 
     def stage_times(self):
         """{stage: (ms, launches)} accumulated since the last call."""
-        ms = (ctypes.c_double * 6)()
-        nl = (ctypes.c_longlong * 6)()
-        self._check(self.L.rihv_stage_times(self.h, ms, nl, 6), self.h)
+        ms = (ctypes.c_double * 7)()
+        nl = (ctypes.c_longlong * 7)()
+        self._check(self.L.rihv_stage_times(self.h, ms, nl, 7), self.h)
         return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
 
     # short aliases

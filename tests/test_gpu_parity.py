@@ -238,8 +238,11 @@ def test_invalid_arguments_are_rejected():
         h.forward(x.data_ptr() + 8, out)        # misaligned
     assert e.value.status == 1
     host = np.zeros(op.shape, np.complex64)
-    with pytest.raises(RihvError):
-        h.forward(host, out)                    # host memory where device is required
+    with pytest.raises(ValueError):
+        h.forward(host, out)                    # the binding refuses host arrays here
+    with pytest.raises(RihvError) as e:
+        h.forward(host.ctypes.data, out)        # and so does the library for raw addresses
+    assert e.value.status == 1
     with pytest.raises(RihvError):
         h.set_options(tv_dims=4)
     with pytest.raises(RihvError):
