@@ -94,6 +94,8 @@ struct rihv_ctx {
   double* trace = nullptr;     // device objective trace
   int trace_cap = 0;
   int* det_err = nullptr;
+  int* tv_err = nullptr;       // set by a TV kernel whose bounded wait gave up
+  CUtensorMap tm_pa[3], tm_pb[3];
   DetectWork det{};
   std::vector<void*> allocs;
 
@@ -263,7 +265,8 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
 rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
   StageScope sc(h, ST_TV, k);
   TvArgs a{};
-  a.v = v;
+  CK(make_volume_tmap(&a.tm_v, v, h->nx, h->ny, h->nz));
+  a.err = h->tv_err;
   a.nx = h->nx;
   a.ny = h->ny;
   a.nz = h->nz;
@@ -273,13 +276,16 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   a.step = 1.f / (4.f * a.dims * mu);
   float2** src = h->pb;
   float2** dst = h->pa;
+  const CUtensorMap* tsrc = h->tm_pb;
+  const CUtensorMap* tdst = h->tm_pa;
   for (int it = 0; it < k; ++it) {
     for (int c = 0; c < 3; ++c) {
-      a.pin[c] = src[c];
+      a.tm_p[c] = tsrc[c];
       a.pout[c] = dst[c];
     }
     CK(launch_tv_step(it == 0, a, h->stream));
     std::swap(src, dst);
+    std::swap(tsrc, tdst);
   }
   *pfinal = src;
   return RIHV_OK;
@@ -396,10 +402,17 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   AL(h->red.partials, 4 * kRedBlocks);
   AL(h->red.tickets, 8);
   AL(h->det_err, 1);
+  AL(h->tv_err, 1);
 #undef AL
   if (cudaMemset(h->red.tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess)
+      cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->tv_err, 0, sizeof(int)) != cudaSuccess)
     return cleanup(fail(h, RIHV_ERR_CUDA, "memset failed"));
+  for (int c = 0; c < 3; ++c) {
+    if (make_volume_tmap(&h->tm_pa[c], h->pa[c], nx, ny, nz) != cudaSuccess ||
+        make_volume_tmap(&h->tm_pb[c], h->pb[c], nx, ny, nz) != cudaSuccess)
+      return cleanup(fail(h, RIHV_ERR_CUDA, "tensor map encoding failed"));
+  }
 
   // Twiddles exp(-2 pi i m / n) in FP64, rounded to float.
   auto twiddles = [](int n) {
@@ -561,6 +574,7 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
       CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
     CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
     CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
+    CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
   }
 
   const float tau = static_cast<float>(h->tau);
@@ -597,9 +611,12 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
   if (trace && check > 0)
     CK(cudaMemcpyAsync(trace, h->trace, sizeof(double) * check, cudaMemcpyDefault, h->stream));
   DevScalars hs{};
+  int tv_err = 0;
   CK(cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&tv_err, h->tv_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (iters_done) *iters_done = done;
+  if (tv_err) return fail(h, RIHV_ERR_TIMEOUT, "a TV kernel's bounded wait gave up");
   if (hs.nonfinite) return fail(h, RIHV_ERR_NONFINITE, "a reduction produced NaN or Inf");
   return RIHV_OK;
 }

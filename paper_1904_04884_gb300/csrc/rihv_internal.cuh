@@ -1,6 +1,7 @@
 // Internal declarations shared by the librihv translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,6 +23,10 @@ constexpr int kMaxPasses = 8;
 constexpr int kTvTx = 32;          // TV tile width (x)
 constexpr int kTvTy = 8;           // TV tile height (y)
 constexpr int kTvThreads = kTvTx * kTvTy;
+constexpr int kTvBoxW = kTvTx + 4; // TMA box width in complex elements (x from i0-2)
+constexpr int kTvBoxH = kTvTy + 2; // TMA box height (y from j0-1)
+constexpr int kTvStages = 4;       // planes in the shared-memory ring
+constexpr int kTvSlotBytes = ((kTvBoxW * kTvBoxH * 8 + 127) / 128) * 128;
 
 constexpr int kRedBlocks = 1216;   // fixed grid of the streaming reduction kernels (8 x 152)
 constexpr int kRedThreads = 256;
@@ -98,15 +103,17 @@ cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, f
 // TV / prox / FISTA kernels (tv_kernels.cu)
 // ---------------------------------------------------------------------------
 struct TvArgs {
-  const float2* v;
-  const float2* pin[3];
-  float2* pout[3];
+  CUtensorMap tm_v;    // v (see make_volume_tmap)
+  CUtensorMap tm_p[3]; // dual input p_x, p_y, p_z
+  float2* pout[3];     // dual output (must not alias the input)
+  int* err;            // set to 1 if a bounded wait gave up
   int nx, ny, nz, dims;
   int zchunk;
   float mu;            // t_tv
   float step;          // 1 / (4 dims mu)
 };
 cudaError_t launch_tv_step(bool first, const TvArgs& a, cudaStream_t s);
+cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz);
 
 enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };
 struct FinArgs {

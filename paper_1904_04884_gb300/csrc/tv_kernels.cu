@@ -8,11 +8,14 @@
 // where (D_x^H p)_i = p_{i-1} [i >= 1] - p_i [i <= n-2] (same along y and z)
 // and Pi scales the voxel's (p_x, p_y, p_z) in C^3 onto the unit ball.
 //
-// k_tv_step marches a 32x8 x-y tile through a chunk of planes (2.5D blocking):
-// plane k+1's p and v are staged in shared memory together with the halo the
-// stencil needs (x-1 for p_x, y-1 for p_y, and plane k for p_z), u is formed
-// for plane k+1 over the tile plus its +x/+y halo, and p' of plane k is
-// written. Each p and v value is read from HBM about once per step.
+// k_tv_step marches a 32x8 x-y tile through a chunk of planes (2.5D blocking).
+// Each plane of v, p_x, p_y, p_z arrives in shared memory as one TMA box
+// (x from i0-2, y from j0-1: the stencil's halo, with the x start kept on a
+// 16-byte boundary; out-of-range boxes are zero filled) into a 4-stage ring
+// completed by mbarriers, so two planes are in flight while one is computed.
+// u is formed for plane k+1 over the tile plus its +x/+y halo, then p' of
+// plane k is written with plain coalesced stores. Every wait is bounded: on
+// timeout the CTA sets the error flag, drains its copies in flight and exits.
 //
 // The finalize kernel forms u = v - mu D^H p, soft-thresholds it, and (in
 // FISTA mode) writes x_k and y_{k+1} = x_k + beta (x_k - x_{k-1}) and reduces
@@ -31,123 +34,188 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 
 constexpr int TX = kTvTx;
 constexpr int TY = kTvTy;
-constexpr int RX = TX + 1;   // region of u: tile plus +x / +y halo
+constexpr int RX = TX + 1;        // region of u: tile plus +x / +y halo
 constexpr int RY = TY + 1;
+constexpr int BW = kTvBoxW;       // TMA box: complex x in [i0-2, i0+TX+2)
+constexpr int BH = kTvBoxH;       //          y in [j0-1, j0+TY]
+constexpr int NSTAGE = kTvStages;
+constexpr int SLOT = kTvSlotBytes;
+constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
 
-struct TvSmem {
-  float2 px[2][RY][TX + 2];  // x in [i0-1, i0+TX], y in [j0, j0+TY]
-  float2 py[2][TY + 2][RX];  // x in [i0, i0+TX],   y in [j0-1, j0+TY]
-  float2 pz[2][RY][RX];      // region
-  float2 v[RY][RX];          // region, plane being formed
-  float2 u[2][RY][RX];       // region, planes k and k+1
+// ---- PTX helpers (TMA + mbarrier) -----------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true if the phase completed, false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* tm, int x, int y, int z,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Shared memory: NSTAGE stages x 4 slots (v, p_x, p_y, p_z) of one box each,
+// then the two u planes, then the mbarriers.
+struct TvLayout {
+  static constexpr int kStageBytes = 4 * SLOT;
+  static constexpr int kUBytes = 2 * RY * RX * 8;
+  static constexpr int kBarOffset = NSTAGE * kStageBytes + kUBytes;
+  static constexpr int kBytes = kBarOffset + NSTAGE * 8;
 };
 
 template <bool FIRST>
-__device__ __forceinline__ void tv_load_plane(TvSmem& sm, const TvArgs& a, int k, int i0, int j0,
-                                              bool load_v, bool load_pxy) {
-  const int b = k & 1;
-  const size_t plane = static_cast<size_t>(k) * a.ny * a.nx;
-  const int tid = threadIdx.x;
-  if (!FIRST) {
-    if (load_pxy) {
-      for (int e = tid; e < RY * (TX + 2); e += kTvThreads) {
-        const int ry = e / (TX + 2), cx = e - ry * (TX + 2);
-        const int gx = i0 - 1 + cx, gy = j0 + ry;
-        float2 val = make_float2(0.f, 0.f);
-        if (gx >= 0 && gx < a.nx && gy < a.ny) val = a.pin[0][plane + static_cast<size_t>(gy) * a.nx + gx];
-        sm.px[b][ry][cx] = val;
-      }
-      for (int e = tid; e < (TY + 2) * RX; e += kTvThreads) {
-        const int ry = e / RX, cx = e - ry * RX;
-        const int gx = i0 + cx, gy = j0 - 1 + ry;
-        float2 val = make_float2(0.f, 0.f);
-        if (gx < a.nx && gy >= 0 && gy < a.ny) val = a.pin[1][plane + static_cast<size_t>(gy) * a.nx + gx];
-        sm.py[b][ry][cx] = val;
-      }
-    }
-    if (a.dims == 3) {
-      for (int e = tid; e < RY * RX; e += kTvThreads) {
-        const int ry = e / RX, cx = e - ry * RX;
-        const int gx = i0 + cx, gy = j0 + ry;
-        float2 val = make_float2(0.f, 0.f);
-        if (gx < a.nx && gy < a.ny) val = a.pin[2][plane + static_cast<size_t>(gy) * a.nx + gx];
-        sm.pz[b][ry][cx] = val;
-      }
-    }
-  }
-  if (load_v) {
-    for (int e = tid; e < RY * RX; e += kTvThreads) {
-      const int ry = e / RX, cx = e - ry * RX;
-      const int gx = i0 + cx, gy = j0 + ry;
-      float2 val = make_float2(0.f, 0.f);
-      if (gx < a.nx && gy < a.ny) val = a.v[plane + static_cast<size_t>(gy) * a.nx + gx];
-      sm.v[ry][cx] = val;
-    }
-  }
-}
-
-// u(k) over the region from the staged p (planes k and k-1) and v (plane k).
-template <bool FIRST>
-__device__ __forceinline__ void tv_form_u(TvSmem& sm, const TvArgs& a, int k, int i0, int j0) {
-  const int b = k & 1;
-  for (int e = threadIdx.x; e < RY * RX; e += kTvThreads) {
-    const int ry = e / RX, cx = e - ry * RX;
-    const int gx = i0 + cx, gy = j0 + ry;
-    float2 u = sm.v[ry][cx];
-    if (!FIRST) {
-      float2 dh = make_float2(0.f, 0.f);
-      if (gx >= 1) dh = cadd(dh, sm.px[b][ry][cx]);
-      if (gx <= a.nx - 2) dh = csub(dh, sm.px[b][ry][cx + 1]);
-      if (gy >= 1) dh = cadd(dh, sm.py[b][ry][cx]);
-      if (gy <= a.ny - 2) dh = csub(dh, sm.py[b][ry + 1][cx]);
-      if (a.dims == 3) {
-        if (k >= 1) dh = cadd(dh, sm.pz[b ^ 1][ry][cx]);
-        if (k <= a.nz - 2) dh = csub(dh, sm.pz[b][ry][cx]);
-      }
-      u = make_float2(u.x - a.mu * dh.x, u.y - a.mu * dh.y);
-    }
-    sm.u[b][ry][cx] = u;
-  }
-}
-
-template <bool FIRST>
 __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ TvArgs a) {
-  __shared__ TvSmem sm;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2(*U)[RY][RX] = reinterpret_cast<float2(*)[RY][RX]>(smem + NSTAGE * TvLayout::kStageBytes);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + TvLayout::kBarOffset);
+
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
   const int gi = i0 + tx, gj = j0 + ty;
+  const int base = zc0 - 1;                // plane held by stage 0, use 0
+  const int qlast = min(zc1, a.nz - 1);    // last plane this CTA needs
+  const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
 
-  // p_z of the plane below the chunk, needed by u(zc0).
-  if (!FIRST && a.dims == 3 && zc0 >= 1) tv_load_plane<FIRST>(sm, a, zc0 - 1, i0, j0, false, false);
-  tv_load_plane<FIRST>(sm, a, zc0, i0, j0, true, true);
+  auto slot = [&](int q, int arr) -> float2(*)[BW] {
+    const int s = (q - base) & (NSTAGE - 1);
+    return reinterpret_cast<float2(*)[BW]>(smem + s * TvLayout::kStageBytes + arr * SLOT);
+  };
+  auto bar_of = [&](int q) { return smem_addr(&bars[(q - base) & (NSTAGE - 1)]); };
+  auto parity_of = [&](int q) { return static_cast<unsigned>(((q - base) / NSTAGE) & 1); };
+  auto issue = [&](int q) {      // thread 0 only
+    const unsigned bar = bar_of(q);
+    mbar_expect_tx(bar, static_cast<unsigned>(nslots * BW * BH * 8));
+    const int x = 2 * (i0 - 2), y = j0 - 1;
+    tma_load_3d(smem_addr(slot(q, 0)), &a.tm_v, x, y, q, bar);
+    if (!FIRST) {
+      tma_load_3d(smem_addr(slot(q, 1)), &a.tm_p[0], x, y, q, bar);
+      tma_load_3d(smem_addr(slot(q, 2)), &a.tm_p[1], x, y, q, bar);
+      if (a.dims == 3) tma_load_3d(smem_addr(slot(q, 3)), &a.tm_p[2], x, y, q, bar);
+    }
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
-  tv_form_u<FIRST>(sm, a, zc0, i0, j0);
+  int issued = base - 1;
+  if (tid == 0) {
+    for (int q = base; q < base + NSTAGE && q <= qlast; ++q) issue(q);
+  }
+  issued = min(base + NSTAGE - 1, qlast);
+  int waited = base - 1;
+
+  // u(k) over the region from stage(k) (p, v) and stage(k-1) (p_z).
+  auto form_u = [&](int k) {
+    float2(*vs)[BW] = slot(k, 0);
+    float2(*px)[BW] = slot(k, 1);
+    float2(*py)[BW] = slot(k, 2);
+    float2(*pz)[BW] = slot(k, 3);
+    float2(*pzm)[BW] = slot(k - 1, 3);
+    float2(*u)[RX] = U[k & 1];
+    for (int e = tid; e < RY * RX; e += kTvThreads) {
+      const int ry = e / RX, rx = e - ry * RX;
+      const int gx = i0 + rx, gy = j0 + ry;
+      const int by = ry + 1, bx = rx + 2;
+      float2 uu = vs[by][bx];
+      if (!FIRST) {
+        float2 dh = make_float2(0.f, 0.f);
+        if (gx >= 1) dh = cadd(dh, px[by][bx - 1]);
+        if (gx <= a.nx - 2) dh = csub(dh, px[by][bx]);
+        if (gy >= 1) dh = cadd(dh, py[by - 1][bx]);
+        if (gy <= a.ny - 2) dh = csub(dh, py[by][bx]);
+        if (a.dims == 3) {
+          if (k >= 1) dh = cadd(dh, pzm[by][bx]);
+          if (k <= a.nz - 2) dh = csub(dh, pz[by][bx]);
+        }
+        uu = make_float2(uu.x - a.mu * dh.x, uu.y - a.mu * dh.y);
+      }
+      u[ry][rx] = uu;
+    }
+  };
+  auto wait_plane = [&](int q) -> bool {
+    const bool ok = mbar_wait(bar_of(q), parity_of(q));
+    return __syncthreads_and(ok) != 0;
+  };
+  auto abort_drain = [&]() {
+    // Record the failure and wait (bounded) for this CTA's copies in flight
+    // before its shared memory is released.
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      for (int q = waited + 1; q <= issued; ++q) mbar_wait(bar_of(q), parity_of(q));
+    }
+    __syncthreads();
+  };
+
+  // prologue: planes base (p_z only) and zc0
+  if (!wait_plane(base)) { abort_drain(); return; }
+  if (!wait_plane(zc0)) { waited = base; abort_drain(); return; }
+  waited = zc0;
+  form_u(zc0);
   __syncthreads();
 
   for (int k = zc0; k < zc1; ++k) {
+    // stage of plane k-1 is free: refill it with plane k+3
+    if (k + 3 <= qlast) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + 3);
+      }
+      issued = k + 3;
+    }
     const bool has_next = (k + 1 < a.nz);
-    if (has_next) tv_load_plane<FIRST>(sm, a, k + 1, i0, j0, true, true);
-    __syncthreads();
-    if (has_next) tv_form_u<FIRST>(sm, a, k + 1, i0, j0);
+    if (has_next) {
+      if (!wait_plane(k + 1)) { abort_drain(); return; }
+      waited = k + 1;
+      form_u(k + 1);
+    }
     __syncthreads();
     if (gi < a.nx && gj < a.ny) {
-      const int b = k & 1;
-      const float2 u0 = sm.u[b][ty][tx];
+      float2(*u)[RX] = U[k & 1];
+      float2(*un)[RX] = U[(k + 1) & 1];
+      const float2 u0 = u[ty][tx];
       float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
-      if (gi <= a.nx - 2) gx = csub(sm.u[b][ty][tx + 1], u0);
-      if (gj <= a.ny - 2) gy = csub(sm.u[b][ty + 1][tx], u0);
-      if (a.dims == 3 && k <= a.nz - 2) gz = csub(sm.u[b ^ 1][ty][tx], u0);
+      if (gi <= a.nx - 2) gx = csub(u[ty][tx + 1], u0);
+      if (gj <= a.ny - 2) gy = csub(u[ty + 1][tx], u0);
+      if (a.dims == 3 && k <= a.nz - 2) gz = csub(un[ty][tx], u0);
       float2 qx, qy, qz;
       if (FIRST) {
         qx = make_float2(a.step * gx.x, a.step * gx.y);
         qy = make_float2(a.step * gy.x, a.step * gy.y);
         qz = make_float2(a.step * gz.x, a.step * gz.y);
       } else {
-        const float2 ox = sm.px[b][ty][tx + 1];
-        const float2 oy = sm.py[b][ty + 1][tx];
-        const float2 oz = (a.dims == 3) ? sm.pz[b][ty][tx] : make_float2(0.f, 0.f);
+        const int by = ty + 1, bx = tx + 2;
+        const float2 ox = slot(k, 1)[by][bx];
+        const float2 oy = slot(k, 2)[by][bx];
+        const float2 oz = (a.dims == 3) ? slot(k, 3)[by][bx] : make_float2(0.f, 0.f);
         qx = make_float2(ox.x + a.step * gx.x, ox.y + a.step * gx.y);
         qy = make_float2(oy.x + a.step * gy.x, oy.y + a.step * gy.y);
         qz = make_float2(oz.x + a.step * gz.x, oz.y + a.step * gz.y);
@@ -361,11 +429,40 @@ int stream_grid(size_t nvox) {
 
 cudaError_t launch_tv_step(bool first, const TvArgs& a, cudaStream_t s) {
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
-  if (first)
-    k_tv_step<true><<<grid, kTvThreads, 0, s>>>(a);
-  else
-    k_tv_step<false><<<grid, kTvThreads, 0, s>>>(a);
+  auto kern = first ? k_tv_step<true> : k_tv_step<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TvLayout::kBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kTvThreads, TvLayout::kBytes, s>>>(a);
   return cudaGetLastError();
+}
+
+// 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box
+// of kTvBoxH rows x 2 kTvBoxW floats x 1 plane, zero fill out of bounds.
+cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(2 * nx), static_cast<cuuint64_t>(ny),
+                              static_cast<cuuint64_t>(nz)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(8) * nx,
+                                 static_cast<cuuint64_t>(8) * nx * ny};
+  const cuuint32_t box[3] = {2 * kTvBoxW, kTvBoxH, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
+                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_finalize(int mode, const FinArgs& a, cudaStream_t s) {
