@@ -6,16 +6,18 @@
 // run the same shared-memory Stockham engine on a tile of B independent
 // transforms stored interleaved, tile[n * (B + 1) + b], so that lanes of a
 // warp that work on the same butterfly index touch consecutive words. Radix
-// 2/3/4/8 butterflies run in registers; twiddles exp(-2 pi i m / n) come from
-// an FP64-computed table staged in shared memory.
+// 2/3/4/8 butterflies run in registers, out of place between two tiles;
+// twiddles exp(-2 pi i m / n) come from an FP64-computed table staged in
+// shared memory. Two CTAs of 512 threads fit on an SM at n = 1024.
 //
 // Between the passes, planes live in a strip-major intermediate layout
 // [z][n_x / W][n_y][W] (W = kStrip) so that one column strip of one plane is a
 // single contiguous block.
 //
 // The forward column pass generates H_j for its strip on the fly from a
-// per-frequency phase table (uint32 fractions of a cycle: phase of plane j is
-// phi0 + j * phid modulo 2^32, exact integer accumulation) and sums over the
+// per-frequency phase table read through L2 (uint32 fractions of a cycle:
+// phase of plane j is phi0 + j * phid modulo 2^32, exact integer
+// accumulation) and sums over the
 // planes of its z-group in registers, so per-plane spectra never reach memory.
 // The adjoint column pass starts from the residual spectrum R, forms
 // conj(H_j) R in registers for every plane and inverse-transforms it.
@@ -110,67 +112,62 @@ struct Dft<3, INV> {
   }
 };
 
-// One in-place Stockham pass of radix R over B interleaved transforms of
-// length n. Every thread first loads all its butterflies' inputs, the block
-// synchronises, then each thread twiddles, transforms and stores.
-// Pass with running product p: butterfly i (k = i mod p) reads
-// x[i + j n/R], multiplies input j by w^(j k), w = exp(-+2 pi i/(p R)), and
-// writes output m to position (i - k) R + k + m p.
-template <int R, int B, int T, int MAXE, bool INV>
-__device__ __forceinline__ void fft_pass(float2* buf, int n, int p, const float2* tw) {
+// One out-of-place Stockham pass of radix R over B interleaved transforms of
+// length n (tile[n * (B + 1) + b]). Butterfly i (k = i mod p, p = product of
+// the radices of earlier passes) reads x[i + j n/R], multiplies input j by
+// w^(j k), w = exp(-+2 pi i/(p R)), transforms, and writes output m to
+// position (i - k) R + k + m p. Threads take butterflies in turn, each holding
+// only its R values, which keeps the register footprint small.
+template <int R, int B, bool INV>
+__device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* __restrict__ out,
+                                         int n, int p, const float2* __restrict__ tw) {
   constexpr int LD = B + 1;
-  constexpr int MAXBF = (MAXE + R - 1) / R;
   const int nr = n / R;
   const int nbf = nr * B;
-  float2 a[MAXBF][R];
-#pragma unroll
-  for (int q = 0; q < MAXBF; ++q) {
-    const int bf = threadIdx.x + q * T;
-    if (bf < nbf) {
-      const int b = bf % B, i = bf / B;
-#pragma unroll
-      for (int j = 0; j < R; ++j) a[q][j] = buf[(i + j * nr) * LD + b];
-    }
-  }
-  __syncthreads();
   const int tstride = n / (p * R);
+  for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+    const int b = bf % B, i = bf / B;
+    float2 v[R];
 #pragma unroll
-  for (int q = 0; q < MAXBF; ++q) {
-    const int bf = threadIdx.x + q * T;
-    if (bf < nbf) {
-      const int b = bf % B, i = bf / B;
-      const int k = i % p;
-      if (p > 1) {
+    for (int j = 0; j < R; ++j) v[j] = in[(i + j * nr) * LD + b];
+    const int k = i % p;
+    if (p > 1) {
 #pragma unroll
-        for (int j = 1; j < R; ++j) {
-          const float2 w = tw[j * k * tstride];
-          a[q][j] = INV ? cmulc(a[q][j], w) : cmul(a[q][j], w);
-        }
+      for (int j = 1; j < R; ++j) {
+        const float2 w = tw[j * k * tstride];
+        v[j] = INV ? cmulc(v[j], w) : cmul(v[j], w);
       }
-      Dft<R, INV>::run(a[q]);
-      const int base = (i - k) * R + k;
-#pragma unroll
-      for (int m = 0; m < R; ++m) buf[(base + m * p) * LD + b] = a[q][m];
     }
+    Dft<R, INV>::run(v);
+    const int base = (i - k) * R + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) out[(base + m * p) * LD + b] = v[m];
   }
   __syncthreads();
 }
 
-template <int B, int T, int MAXE, bool INV>
-__device__ __forceinline__ void fft_run(float2* buf, const FftPlan& plan, const float2* tw) {
+// Runs all passes of the plan, ping-ponging between two tiles; returns the
+// tile holding the result.
+template <int B, bool INV>
+__device__ __forceinline__ float2* fft_run(float2* t0, float2* t1, const FftPlan& plan,
+                                           const float2* tw) {
   int p = 1;
   for (int s = 0; s < plan.npass; ++s) {
     const int r = plan.radix[s];
     if (r == 8)
-      fft_pass<8, B, T, MAXE, INV>(buf, plan.n, p, tw);
+      fft_pass<8, B, INV>(t0, t1, plan.n, p, tw);
     else if (r == 4)
-      fft_pass<4, B, T, MAXE, INV>(buf, plan.n, p, tw);
+      fft_pass<4, B, INV>(t0, t1, plan.n, p, tw);
     else if (r == 2)
-      fft_pass<2, B, T, MAXE, INV>(buf, plan.n, p, tw);
+      fft_pass<2, B, INV>(t0, t1, plan.n, p, tw);
     else
-      fft_pass<3, B, T, MAXE, INV>(buf, plan.n, p, tw);
+      fft_pass<3, B, INV>(t0, t1, plan.n, p, tw);
     p *= r;
+    float2* t = t0;
+    t0 = t1;
+    t1 = t;
   }
+  return t0;
 }
 
 __device__ __forceinline__ void stage_twiddles(float2* dst, const float2* src, int n) {
@@ -182,65 +179,72 @@ __device__ __forceinline__ void stage_twiddles(float2* dst, const float2* src, i
 // grid (ny / kRowsPerCta, nz)
 // ---------------------------------------------------------------------------
 template <bool INV, int IN, int OUT, int EPI>
-__global__ void __launch_bounds__(kFftThreads) k_rows(const __grid_constant__ RowArgs a) {
+__global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__ RowArgs a) {
   constexpr int B = kRowsPerCta;
   constexpr int LD = B + 1;
   constexpr int T = kFftThreads;
-  constexpr int MAXE = kMaxN * B / T;
   constexpr int W = kStrip;
   extern __shared__ float2 smem[];
   const int n = a.nx;
   float2* tile = smem;
-  float2* tw = smem + n * LD;
+  float2* tile2 = smem + n * LD;
+  float2* tw = smem + 2 * n * LD;
   stage_twiddles(tw, a.tw, n);
 
-  const int r0 = blockIdx.x * B;
-  const size_t z = blockIdx.y;
   const int nstrip = a.nx / W;
   const int total = B * n;
-
-  // Load B rows, transposed into the interleaved tile.
-  for (int e = threadIdx.x; e < total; e += T) {
-    int rl, col;
-    float2 val;
-    if (IN == ROW_IN_STRIP) {
-      const int s = e / (B * W), w = e - s * (B * W);
-      rl = w / W;
-      col = s * W + (w - rl * W);
-      const float2* src = static_cast<const float2*>(a.src);
-      val = src[((z * nstrip + s) * a.ny + r0) * W + w];
-    } else {
-      rl = e / n;
-      col = e - rl * n;
-      const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
-      if (IN == ROW_IN_F32)
-        val = make_float2(static_cast<const float*>(a.src)[gi], 0.f);
-      else
-        val = static_cast<const float2*>(a.src)[gi];
-    }
-    tile[col * LD + rl] = val;
-  }
+  const int rblocks = a.ny / B;
+  const int nitems = rblocks * a.nz;
   __syncthreads();
 
-  fft_run<B, T, MAXE, INV>(tile, a.plan, tw);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int r0 = (item % rblocks) * B;
+    const size_t z = item / rblocks;
 
-  for (int e = threadIdx.x; e < total; e += T) {
-    if (OUT == ROW_OUT_STRIP) {
-      const int s = e / (B * W), w = e - s * (B * W);
-      const int rl = w / W;
-      const int col = s * W + (w - rl * W);
-      a.dst[((z * nstrip + s) * a.ny + r0) * W + w] = cscale(tile[col * LD + rl], a.scale);
-    } else {
-      const int rl = e / n, col = e - rl * n;
-      const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
-      const float2 g = tile[col * LD + rl];
-      if (EPI == ROW_EPI_GRAD) {
-        const float2 y = a.y[gi];
-        a.dst[gi] = make_float2(y.x - a.scale * g.x, y.y - a.scale * g.y);
+    // Load B rows, transposed into the interleaved tile.
+    for (int e = threadIdx.x; e < total; e += T) {
+      int rl, col;
+      float2 val;
+      if (IN == ROW_IN_STRIP) {
+        const int s = e / (B * W), w = e - s * (B * W);
+        rl = w / W;
+        col = s * W + (w - rl * W);
+        const float2* src = static_cast<const float2*>(a.src);
+        val = src[((z * nstrip + s) * a.ny + r0) * W + w];
       } else {
-        a.dst[gi] = cscale(g, a.scale);
+        rl = e / n;
+        col = e - rl * n;
+        const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
+        if (IN == ROW_IN_F32)
+          val = make_float2(static_cast<const float*>(a.src)[gi], 0.f);
+        else
+          val = static_cast<const float2*>(a.src)[gi];
+      }
+      tile[col * LD + rl] = val;
+    }
+    __syncthreads();
+
+    const float2* res = fft_run<B, INV>(tile, tile2, a.plan, tw);
+
+    for (int e = threadIdx.x; e < total; e += T) {
+      if (OUT == ROW_OUT_STRIP) {
+        const int s = e / (B * W), w = e - s * (B * W);
+        const int rl = w / W;
+        const int col = s * W + (w - rl * W);
+        a.dst[((z * nstrip + s) * a.ny + r0) * W + w] = cscale(res[col * LD + rl], a.scale);
+      } else {
+        const int rl = e / n, col = e - rl * n;
+        const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
+        const float2 g = res[col * LD + rl];
+        if (EPI == ROW_EPI_GRAD) {
+          const float2 y = a.y[gi];
+          a.dst[gi] = make_float2(y.x - a.scale * g.x, y.y - a.scale * g.y);
+        } else {
+          a.dst[gi] = cscale(g, a.scale);
+        }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -257,7 +261,7 @@ __device__ __forceinline__ float2 transfer(uint2 ph, float amp, int j) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ ColArgs a) {
+__global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__ ColArgs a) {
   constexpr int B = kStrip;
   constexpr int LD = B + 1;
   constexpr int T = kFftThreads;
@@ -266,23 +270,15 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ Co
   const int n = a.ny;
   const int elems = n * B;
   float2* tile = smem;
-  float2* tw = smem + n * LD;
-  uint2* ph_s = reinterpret_cast<uint2*>(tw + n);
-  float* amp_s = reinterpret_cast<float*>(ph_s + elems);
+  float2* tile2 = smem + n * LD;
+  float2* tw = smem + 2 * n * LD;
   stage_twiddles(tw, a.tw, n);
 
   const int s = blockIdx.x;
   const int nstrip = a.nx / B;
   const size_t strip_elems = static_cast<size_t>(elems);
-
-  if (MODE == COL_FWD_ZSUM || MODE == COL_ADJ_GEN) {
-    const uint2* ph_g = a.phase + s * strip_elems;
-    const float* amp_g = a.amp + s * strip_elems;
-    for (int e = threadIdx.x; e < elems; e += T) {
-      ph_s[e] = ph_g[e];
-      amp_s[e] = amp_g[e];
-    }
-  }
+  const uint2* ph_g = a.phase + s * strip_elems;
+  const float* amp_g = a.amp + s * strip_elems;
   __syncthreads();
 
   if (MODE == COL_FWD_ZSUM) {
@@ -298,15 +294,14 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ Co
         tile[r * LD + (e - r * B)] = src[e];
       }
       __syncthreads();
-      fft_run<B, T, MAXE, false>(tile, a.plan, tw);
+      const float2* res = fft_run<B, false>(tile, tile2, a.plan, tw);
 #pragma unroll
       for (int q = 0; q < MAXE; ++q) {
         const int e = threadIdx.x + q * T;
         if (e < elems) {
           const int r = e / B;
-          const float2 h = transfer(ph_s[e], amp_s[e], z);
-          const float2 v = tile[r * LD + (e - r * B)];
-          acc[q] = cadd(acc[q], cmul(h, v));
+          const float2 h = transfer(__ldg(ph_g + e), __ldg(amp_g + e), z);
+          acc[q] = cadd(acc[q], cmul(h, res[r * LD + (e - r * B)]));
         }
       }
       __syncthreads();
@@ -339,16 +334,16 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ Co
         const int e = threadIdx.x + q * T;
         if (e < elems) {
           const int r = e / B;
-          const float2 h = transfer(ph_s[e], amp_s[e], z);
+          const float2 h = transfer(__ldg(ph_g + e), __ldg(amp_g + e), z);
           tile[r * LD + (e - r * B)] = cmulc(rr[q], h);
         }
       }
       __syncthreads();
-      fft_run<B, T, MAXE, true>(tile, a.plan, tw);
+      const float2* res = fft_run<B, true>(tile, tile2, a.plan, tw);
       float2* dst = a.dst + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
       for (int e = threadIdx.x; e < elems; e += T) {
         const int r = e / B;
-        dst[e] = tile[r * LD + (e - r * B)];
+        dst[e] = res[r * LD + (e - r * B)];
       }
       __syncthreads();
     }
@@ -360,11 +355,11 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ Co
       tile[r * LD + (e - r * B)] = src[e];
     }
     __syncthreads();
-    fft_run<B, T, MAXE, false>(tile, a.plan, tw);
+    const float2* res = fft_run<B, false>(tile, tile2, a.plan, tw);
     for (int e = threadIdx.x; e < elems; e += T) {
       const int r = e / B;
       a.dst[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)] =
-          cscale(tile[r * LD + (e - r * B)], a.scale);
+          cscale(res[r * LD + (e - r * B)], a.scale);
     }
   } else {  // COL_PLAIN_INV: row-major spectrum -> strip-major plane 0
     for (int e = threadIdx.x; e < elems; e += T) {
@@ -372,11 +367,11 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(const __grid_constant__ Co
       tile[r * LD + (e - r * B)] = a.src[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)];
     }
     __syncthreads();
-    fft_run<B, T, MAXE, true>(tile, a.plan, tw);
+    const float2* res = fft_run<B, true>(tile, tile2, a.plan, tw);
     float2* dst = a.dst + static_cast<size_t>(s) * strip_elems;
     for (int e = threadIdx.x; e < elems; e += T) {
       const int r = e / B;
-      dst[e] = cscale(tile[r * LD + (e - r * B)], a.scale);
+      dst[e] = cscale(res[r * LD + (e - r * B)], a.scale);
     }
   }
 }
@@ -442,7 +437,11 @@ cudaError_t launch_rows_t(const RowArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  dim3 grid(a.ny / kRowsPerCta, a.nz);
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = (a.ny / kRowsPerCta) * a.nz;
+  const int grid = items < 4 * sms ? items : 4 * sms;
   kern<<<grid, kFftThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -462,14 +461,12 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 }  // namespace
 
 size_t rows_smem_bytes(int nx) {
-  return sizeof(float2) * (static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
+  return sizeof(float2) * (2 * static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
 }
 
 size_t cols_smem_bytes(int mode, int ny) {
-  size_t b = sizeof(float2) * (static_cast<size_t>(ny) * (kStrip + 1) + ny);
-  if (mode == COL_FWD_ZSUM || mode == COL_ADJ_GEN)
-    b += static_cast<size_t>(ny) * kStrip * (sizeof(uint2) + sizeof(float));
-  return b;
+  (void)mode;
+  return sizeof(float2) * (2 * static_cast<size_t>(ny) * (kStrip + 1) + ny);
 }
 
 cudaError_t launch_rows(int inv, int in, int out, int epi, const RowArgs& a, cudaStream_t s) {
