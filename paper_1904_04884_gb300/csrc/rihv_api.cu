@@ -263,7 +263,9 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
 
 // K dual steps; returns the buffer set holding the final p.
 rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
-  StageScope sc(h, ST_TV, k);
+  // Two dual steps per launch; a single-step launch finishes an odd count.
+  const int launches = k / 2 + (k % 2);
+  StageScope sc(h, ST_TV, launches);
   TvArgs a{};
   CK(make_volume_tmap(&a.tm_v, v, h->nx, h->ny, h->nz));
   a.err = h->tv_err;
@@ -278,12 +280,15 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   float2** dst = h->pa;
   const CUtensorMap* tsrc = h->tm_pb;
   const CUtensorMap* tdst = h->tm_pa;
-  for (int it = 0; it < k; ++it) {
+  int done = 0;
+  while (done < k) {
+    const int n = (k - done >= 2) ? 2 : 1;
     for (int c = 0; c < 3; ++c) {
       a.tm_p[c] = tsrc[c];
       a.pout[c] = dst[c];
     }
-    CK(launch_tv_step(it == 0, a, h->stream));
+    CK(launch_tv_step(done == 0, n, a, h->stream));
+    done += n;
     std::swap(src, dst);
     std::swap(tsrc, tdst);
   }

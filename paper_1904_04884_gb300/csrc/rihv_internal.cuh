@@ -24,7 +24,7 @@ constexpr int kTvTx = 32;          // TV tile width (x)
 constexpr int kTvTy = 8;           // TV tile height (y)
 constexpr int kTvThreads = kTvTx * kTvTy;
 constexpr int kTvBoxW = kTvTx + 4; // TMA box width in complex elements (x from i0-2)
-constexpr int kTvBoxH = kTvTy + 2; // TMA box height (y from j0-1)
+constexpr int kTvBoxH = kTvTy + 4; // TMA box height (y from j0-2)
 constexpr int kTvStages = 4;       // planes in the shared-memory ring
 constexpr int kTvSlotBytes = ((kTvBoxW * kTvBoxH * 8 + 127) / 128) * 128;
 
@@ -112,7 +112,8 @@ struct TvArgs {
   float mu;            // t_tv
   float step;          // 1 / (4 dims mu)
 };
-cudaError_t launch_tv_step(bool first, const TvArgs& a, cudaStream_t s);
+// nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero.
+cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s);
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz);
 
 enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };

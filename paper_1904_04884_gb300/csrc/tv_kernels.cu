@@ -8,14 +8,16 @@
 // where (D_x^H p)_i = p_{i-1} [i >= 1] - p_i [i <= n-2] (same along y and z)
 // and Pi scales the voxel's (p_x, p_y, p_z) in C^3 onto the unit ball.
 //
-// k_tv_step marches a 32x8 x-y tile through a chunk of planes (2.5D blocking).
-// Each plane of v, p_x, p_y, p_z arrives in shared memory as one TMA box
-// (x from i0-2, y from j0-1: the stencil's halo, with the x start kept on a
-// 16-byte boundary; out-of-range boxes are zero filled) into a 4-stage ring
-// completed by mbarriers, so two planes are in flight while one is computed.
-// u is formed for plane k+1 over the tile plus its +x/+y halo, then p' of
-// plane k is written with plain coalesced stores. Every wait is bounded: on
-// timeout the CTA sets the error flag, drains its copies in flight and exits.
+// The TV kernels march a 32x8 x-y tile through a chunk of planes (2.5D
+// blocking). Each plane of v, p_x, p_y, p_z arrives in shared memory as one
+// TMA box (x from i0-2, y from j0-2: the stencil's halo, with the x start kept
+// on a 16-byte boundary; out-of-range boxes are zero filled) into a 4-stage
+// ring completed by mbarriers, so two planes are in flight while one is
+// computed. k_tv_step2 performs two dual steps per launch (temporal blocking,
+// first step recomputed on a halo ring in shared memory); k_tv_step performs
+// one (for odd step counts). Outputs go out with plain coalesced stores. Every
+// wait is bounded: on timeout the CTA sets the error flag, drains its copies
+// in flight and exits.
 //
 // The finalize kernel forms u = v - mu D^H p, soft-thresholds it, and (in
 // FISTA mode) writes x_k and y_{k+1} = x_k + beta (x_k - x_{k-1}) and reduces
@@ -34,13 +36,20 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 
 constexpr int TX = kTvTx;
 constexpr int TY = kTvTy;
-constexpr int RX = TX + 1;        // region of u: tile plus +x / +y halo
-constexpr int RY = TY + 1;
 constexpr int BW = kTvBoxW;       // TMA box: complex x in [i0-2, i0+TX+2)
-constexpr int BH = kTvBoxH;       //          y in [j0-1, j0+TY]
+constexpr int BH = kTvBoxH;       //          y in [j0-2, j0+TY+2)
 constexpr int NSTAGE = kTvStages;
 constexpr int SLOT = kTvSlotBytes;
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
+
+// Regions (x extent, y extent) relative to the tile origin (i0, j0):
+//   A  = u of the first step:   x in [-1, TX+1], y in [-1, TY+1]
+//   R2 = p of the first step:   x in [-1, TX],   y in [-1, TY]
+//   R1 = u of the last step:    x in [0, TX],    y in [0, TY]
+//   T  = output tile:           x in [0, TX),    y in [0, TY)
+constexpr int AX = TX + 3, AY = TY + 3;
+constexpr int R2X = TX + 2, R2Y = TY + 2;
+constexpr int R1X = TX + 1, R1Y = TY + 1;
 
 // ---- PTX helpers (TMA + mbarrier) -----------------------------------------
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -78,159 +87,335 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* tm,
       : "memory");
 }
 
-// Shared memory: NSTAGE stages x 4 slots (v, p_x, p_y, p_z) of one box each,
-// then the two u planes, then the mbarriers.
-struct TvLayout {
-  static constexpr int kStageBytes = 4 * SLOT;
-  static constexpr int kUBytes = 2 * RY * RX * 8;
-  static constexpr int kBarOffset = NSTAGE * kStageBytes + kUBytes;
-  static constexpr int kBytes = kBarOffset + NSTAGE * 8;
+__device__ __forceinline__ float2 fma2(float2 a, float s, float2 g) {
+  return make_float2(a.x + s * g.x, a.y + s * g.y);
+}
+
+// Projection of (qx, qy, qz) onto the unit ball of C^3.
+__device__ __forceinline__ void project(float2& qx, float2& qy, float2& qz) {
+  const float n2 = qx.x * qx.x + qx.y * qx.y + qy.x * qy.x + qy.y * qy.y + qz.x * qz.x + qz.y * qz.y;
+  if (n2 > 1.f) {
+    const float sc = rsqrtf(n2);
+    qx.x *= sc; qx.y *= sc; qy.x *= sc; qy.y *= sc; qz.x *= sc; qz.y *= sc;
+  }
+}
+
+// Plane ring fed by TMA: NSTAGE stages x 4 slots (v, p_x, p_y, p_z). Plane q
+// lives in stage (q - base) mod NSTAGE; its n-th use has mbarrier parity n&1.
+struct PlaneRing {
+  unsigned char* smem;
+  unsigned long long* bars;
+  int base;
+  __device__ float2 (*slot(int q, int arr) const)[BW] {
+    const int s = (q - base) & (NSTAGE - 1);
+    return reinterpret_cast<float2(*)[BW]>(smem + (s * 4 + arr) * SLOT);
+  }
+  __device__ unsigned bar(int q) const { return smem_addr(&bars[(q - base) & (NSTAGE - 1)]); }
+  __device__ unsigned parity(int q) const { return static_cast<unsigned>(((q - base) / NSTAGE) & 1); }
 };
 
 template <bool FIRST>
+__device__ __forceinline__ void ring_issue(const PlaneRing& r, const TvArgs& a, int q, int i0,
+                                           int j0) {
+  const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
+  const unsigned bar = r.bar(q);
+  mbar_expect_tx(bar, static_cast<unsigned>(nslots * BW * BH * 8));
+  const int x = 2 * (i0 - 2), y = j0 - 2;
+  tma_load_3d(smem_addr(r.slot(q, 0)), &a.tm_v, x, y, q, bar);
+  if (!FIRST) {
+    tma_load_3d(smem_addr(r.slot(q, 1)), &a.tm_p[0], x, y, q, bar);
+    tma_load_3d(smem_addr(r.slot(q, 2)), &a.tm_p[1], x, y, q, bar);
+    if (a.dims == 3) tma_load_3d(smem_addr(r.slot(q, 3)), &a.tm_p[2], x, y, q, bar);
+  }
+}
+
+// Block-uniform bounded wait for plane q.
+__device__ __forceinline__ bool ring_wait(const PlaneRing& r, int q) {
+  const bool ok = mbar_wait(r.bar(q), r.parity(q));
+  return __syncthreads_and(ok) != 0;
+}
+
+// Records a failed wait and drains this CTA's copies in flight (bounded)
+// before its shared memory is released.
+__device__ __forceinline__ void ring_abort(const PlaneRing& r, const TvArgs& a, int waited,
+                                           int issued) {
+  if (threadIdx.x == 0) {
+    atomicExch(a.err, 1);
+    for (int q = waited + 1; q <= issued; ++q) mbar_wait(r.bar(q), r.parity(q));
+  }
+  __syncthreads();
+}
+
+// u = v - mu D^H p at global (gx, gy) of plane k, reading the staged box at
+// (by, bx) for plane k and the p_z of plane k-1 from `pzm`.
+template <bool FIRST>
+__device__ __forceinline__ float2 u_from_box(const TvArgs& a, float2 (*vs)[BW], float2 (*px)[BW],
+                                             float2 (*py)[BW], float2 (*pz)[BW],
+                                             float2 (*pzm)[BW], int by, int bx, int gx, int gy,
+                                             int k) {
+  float2 uu = vs[by][bx];
+  if (!FIRST) {
+    float2 dh = make_float2(0.f, 0.f);
+    if (gx >= 1) dh = cadd(dh, px[by][bx - 1]);
+    if (gx <= a.nx - 2) dh = csub(dh, px[by][bx]);
+    if (gy >= 1) dh = cadd(dh, py[by - 1][bx]);
+    if (gy <= a.ny - 2) dh = csub(dh, py[by][bx]);
+    if (a.dims == 3) {
+      if (k >= 1) dh = cadd(dh, pzm[by][bx]);
+      if (k <= a.nz - 2) dh = csub(dh, pz[by][bx]);
+    }
+    uu = make_float2(uu.x - a.mu * dh.x, uu.y - a.mu * dh.y);
+  }
+  return uu;
+}
+
+struct TvLayout1 {   // one dual step per launch
+  static constexpr int kUBytes = 2 * R1Y * R1X * 8;
+  static constexpr int kBarOffset = NSTAGE * 4 * SLOT + kUBytes;
+  static constexpr int kBytes = kBarOffset + NSTAGE * 8;
+};
+
+// One dual gradient-projection step (used for an odd step count).
+template <bool FIRST>
 __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ TvArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float2(*U)[RY][RX] = reinterpret_cast<float2(*)[RY][RX]>(smem + NSTAGE * TvLayout::kStageBytes);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + TvLayout::kBarOffset);
-
+  float2(*U)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + NSTAGE * 4 * SLOT);
+  PlaneRing ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout1::kBarOffset),
+                 static_cast<int>(blockIdx.z) * a.zchunk - 1};
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int gi = i0 + tx, gj = j0 + ty;
-  const int base = zc0 - 1;                // plane held by stage 0, use 0
-  const int qlast = min(zc1, a.nz - 1);    // last plane this CTA needs
-  const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
-
-  auto slot = [&](int q, int arr) -> float2(*)[BW] {
-    const int s = (q - base) & (NSTAGE - 1);
-    return reinterpret_cast<float2(*)[BW]>(smem + s * TvLayout::kStageBytes + arr * SLOT);
-  };
-  auto bar_of = [&](int q) { return smem_addr(&bars[(q - base) & (NSTAGE - 1)]); };
-  auto parity_of = [&](int q) { return static_cast<unsigned>(((q - base) / NSTAGE) & 1); };
-  auto issue = [&](int q) {      // thread 0 only
-    const unsigned bar = bar_of(q);
-    mbar_expect_tx(bar, static_cast<unsigned>(nslots * BW * BH * 8));
-    const int x = 2 * (i0 - 2), y = j0 - 1;
-    tma_load_3d(smem_addr(slot(q, 0)), &a.tm_v, x, y, q, bar);
-    if (!FIRST) {
-      tma_load_3d(smem_addr(slot(q, 1)), &a.tm_p[0], x, y, q, bar);
-      tma_load_3d(smem_addr(slot(q, 2)), &a.tm_p[1], x, y, q, bar);
-      if (a.dims == 3) tma_load_3d(smem_addr(slot(q, 3)), &a.tm_p[2], x, y, q, bar);
-    }
-  };
+  const int qlast = min(zc1, a.nz - 1);
 
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int issued = base - 1;
-  if (tid == 0) {
-    for (int q = base; q < base + NSTAGE && q <= qlast; ++q) issue(q);
-  }
-  issued = min(base + NSTAGE - 1, qlast);
-  int waited = base - 1;
+  if (tid == 0)
+    for (int q = ring.base; q < ring.base + NSTAGE && q <= qlast; ++q) ring_issue<FIRST>(ring, a, q, i0, j0);
+  int issued = min(ring.base + NSTAGE - 1, qlast);
+  int waited = ring.base - 1;
 
-  // u(k) over the region from stage(k) (p, v) and stage(k-1) (p_z).
   auto form_u = [&](int k) {
-    float2(*vs)[BW] = slot(k, 0);
-    float2(*px)[BW] = slot(k, 1);
-    float2(*py)[BW] = slot(k, 2);
-    float2(*pz)[BW] = slot(k, 3);
-    float2(*pzm)[BW] = slot(k - 1, 3);
-    float2(*u)[RX] = U[k & 1];
-    for (int e = tid; e < RY * RX; e += kTvThreads) {
-      const int ry = e / RX, rx = e - ry * RX;
-      const int gx = i0 + rx, gy = j0 + ry;
-      const int by = ry + 1, bx = rx + 2;
-      float2 uu = vs[by][bx];
-      if (!FIRST) {
-        float2 dh = make_float2(0.f, 0.f);
-        if (gx >= 1) dh = cadd(dh, px[by][bx - 1]);
-        if (gx <= a.nx - 2) dh = csub(dh, px[by][bx]);
-        if (gy >= 1) dh = cadd(dh, py[by - 1][bx]);
-        if (gy <= a.ny - 2) dh = csub(dh, py[by][bx]);
-        if (a.dims == 3) {
-          if (k >= 1) dh = cadd(dh, pzm[by][bx]);
-          if (k <= a.nz - 2) dh = csub(dh, pz[by][bx]);
-        }
-        uu = make_float2(uu.x - a.mu * dh.x, uu.y - a.mu * dh.y);
-      }
-      u[ry][rx] = uu;
+    float2(*u)[R1X] = U[k & 1];
+    for (int e = tid; e < R1Y * R1X; e += kTvThreads) {
+      const int ry = e / R1X, rx = e - ry * R1X;
+      u[ry][rx] = u_from_box<FIRST>(a, ring.slot(k, 0), ring.slot(k, 1), ring.slot(k, 2),
+                                    ring.slot(k, 3), ring.slot(k - 1, 3), ry + 2, rx + 2, i0 + rx,
+                                    j0 + ry, k);
     }
-  };
-  auto wait_plane = [&](int q) -> bool {
-    const bool ok = mbar_wait(bar_of(q), parity_of(q));
-    return __syncthreads_and(ok) != 0;
-  };
-  auto abort_drain = [&]() {
-    // Record the failure and wait (bounded) for this CTA's copies in flight
-    // before its shared memory is released.
-    if (tid == 0) {
-      atomicExch(a.err, 1);
-      for (int q = waited + 1; q <= issued; ++q) mbar_wait(bar_of(q), parity_of(q));
-    }
-    __syncthreads();
   };
 
-  // prologue: planes base (p_z only) and zc0
-  if (!wait_plane(base)) { abort_drain(); return; }
-  if (!wait_plane(zc0)) { waited = base; abort_drain(); return; }
+  if (!ring_wait(ring, ring.base)) { ring_abort(ring, a, waited, issued); return; }
+  waited = ring.base;
+  if (!ring_wait(ring, zc0)) { ring_abort(ring, a, waited, issued); return; }
   waited = zc0;
   form_u(zc0);
   __syncthreads();
 
   for (int k = zc0; k < zc1; ++k) {
-    // stage of plane k-1 is free: refill it with plane k+3
-    if (k + 3 <= qlast) {
+    if (k + 3 <= qlast) {     // stage of plane k-1 is free
       if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(k + 3);
+        ring_issue<FIRST>(ring, a, k + 3, i0, j0);
       }
       issued = k + 3;
     }
     const bool has_next = (k + 1 < a.nz);
     if (has_next) {
-      if (!wait_plane(k + 1)) { abort_drain(); return; }
+      if (!ring_wait(ring, k + 1)) { ring_abort(ring, a, waited, issued); return; }
       waited = k + 1;
       form_u(k + 1);
     }
     __syncthreads();
     if (gi < a.nx && gj < a.ny) {
-      float2(*u)[RX] = U[k & 1];
-      float2(*un)[RX] = U[(k + 1) & 1];
+      float2(*u)[R1X] = U[k & 1];
+      float2(*un)[R1X] = U[(k + 1) & 1];
       const float2 u0 = u[ty][tx];
       float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
       if (gi <= a.nx - 2) gx = csub(u[ty][tx + 1], u0);
       if (gj <= a.ny - 2) gy = csub(u[ty + 1][tx], u0);
       if (a.dims == 3 && k <= a.nz - 2) gz = csub(un[ty][tx], u0);
-      float2 qx, qy, qz;
-      if (FIRST) {
-        qx = make_float2(a.step * gx.x, a.step * gx.y);
-        qy = make_float2(a.step * gy.x, a.step * gy.y);
-        qz = make_float2(a.step * gz.x, a.step * gz.y);
-      } else {
-        const int by = ty + 1, bx = tx + 2;
-        const float2 ox = slot(k, 1)[by][bx];
-        const float2 oy = slot(k, 2)[by][bx];
-        const float2 oz = (a.dims == 3) ? slot(k, 3)[by][bx] : make_float2(0.f, 0.f);
-        qx = make_float2(ox.x + a.step * gx.x, ox.y + a.step * gx.y);
-        qy = make_float2(oy.x + a.step * gy.x, oy.y + a.step * gy.y);
-        qz = make_float2(oz.x + a.step * gz.x, oz.y + a.step * gz.y);
+      float2 qx = make_float2(0.f, 0.f), qy = qx, qz = qx;
+      if (!FIRST) {
+        qx = ring.slot(k, 1)[ty + 2][tx + 2];
+        qy = ring.slot(k, 2)[ty + 2][tx + 2];
+        if (a.dims == 3) qz = ring.slot(k, 3)[ty + 2][tx + 2];
       }
-      const float n2 = qx.x * qx.x + qx.y * qx.y + qy.x * qy.x + qy.y * qy.y + qz.x * qz.x + qz.y * qz.y;
-      if (n2 > 1.f) {
-        const float sc = rsqrtf(n2);
-        qx.x *= sc; qx.y *= sc; qy.x *= sc; qy.y *= sc; qz.x *= sc; qz.y *= sc;
-      }
+      qx = fma2(qx, a.step, gx);
+      qy = fma2(qy, a.step, gy);
+      qz = fma2(qz, a.step, gz);
+      project(qx, qy, qz);
       const size_t gidx = (static_cast<size_t>(k) * a.ny + gj) * a.nx + gi;
       a.pout[0][gidx] = qx;
       a.pout[1][gidx] = qy;
       if (a.dims == 3) a.pout[2][gidx] = qz;
     }
     __syncthreads();
+  }
+}
+
+struct TvLayout2 {   // two dual steps per launch
+  static constexpr int kU0Off = NSTAGE * 4 * SLOT;
+  static constexpr int kU0Bytes = 2 * AY * AX * 8;
+  static constexpr int kP1Off = kU0Off + kU0Bytes;
+  static constexpr int kP1Bytes = 2 * 3 * R2Y * R2X * 8;
+  static constexpr int kU1Off = kP1Off + kP1Bytes;
+  static constexpr int kU1Bytes = 2 * R1Y * R1X * 8;
+  static constexpr int kBarOffset = kU1Off + kU1Bytes;
+  static constexpr int kBytes = kBarOffset + NSTAGE * 8;
+};
+
+// Two dual gradient-projection steps per launch (temporal blocking). With p^0
+// the input dual and p^2 the output, per plane tick t of the z march:
+//   (a) u^0(t+1) over A   from p^0(t+1), p^0_z(t), v(t+1)   [TMA ring]
+//   (b) p^1(t)   over R2  from u^0(t), u^0(t+1), p^0(t)
+//   (c) u^1(t)   over R1  from p^1(t), p^1_z(t-1), v(t)
+//   (d) p^2(t-1) over T   from u^1(t-1), u^1(t), p^1(t-1)   -> global
+// Step 1 is recomputed on a one-voxel halo ring around the tile (R2), which
+// needs a two-voxel halo of p^0 and v: the TMA box covers x in [i0-2, i0+TX+2)
+// and y in [j0-2, j0+TY+2). HBM traffic per voxel for two steps is one read of
+// v and p^0 and one write of p^2.
+template <bool FIRST>
+__global__ void __launch_bounds__(kTvThreads, 2) k_tv_step2(const __grid_constant__ TvArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2(*U0)[AY][AX] = reinterpret_cast<float2(*)[AY][AX]>(smem + TvLayout2::kU0Off);
+  float2(*P1)[3][R2Y][R2X] = reinterpret_cast<float2(*)[3][R2Y][R2X]>(smem + TvLayout2::kP1Off);
+  float2(*U1)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + TvLayout2::kU1Off);
+  const int zc0 = blockIdx.z * a.zchunk;
+  const int zc1 = min(a.nz, zc0 + a.zchunk);
+  // planes zc0-2 .. zc1+1 are read (out-of-range planes arrive zero filled)
+  PlaneRing ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset), zc0 - 2};
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  const int qlast = zc1 + 1;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int q = ring.base; q < ring.base + NSTAGE && q <= qlast; ++q) ring_issue<FIRST>(ring, a, q, i0, j0);
+  int issued = min(ring.base + NSTAGE - 1, qlast);
+  int waited = ring.base - 1;
+
+  // (a) u^0(q) over A (box coordinates: A origin is box (1, 1))
+  auto step_a = [&](int q) {
+    float2(*u)[AX] = U0[q & 1];
+    for (int e = tid; e < AY * AX; e += kTvThreads) {
+      const int ry = e / AX, rx = e - ry * AX;
+      u[ry][rx] = u_from_box<FIRST>(a, ring.slot(q, 0), ring.slot(q, 1), ring.slot(q, 2),
+                                    ring.slot(q, 3), ring.slot(q - 1, 3), ry + 1, rx + 1,
+                                    i0 - 1 + rx, j0 - 1 + ry, q);
+    }
+  };
+  // (b) p^1(q) over R2 (R2 origin is A (0, 0) and box (1, 1))
+  auto step_b = [&](int q) {
+    float2(*u)[AX] = U0[q & 1];
+    float2(*un)[AX] = U0[(q + 1) & 1];
+    float2(*p1)[R2Y][R2X] = P1[q & 1];
+    for (int e = tid; e < R2Y * R2X; e += kTvThreads) {
+      const int ry = e / R2X, rx = e - ry * R2X;
+      const int gx = i0 - 1 + rx, gy = j0 - 1 + ry;
+      const float2 u0 = u[ry][rx];
+      float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
+      if (gx <= a.nx - 2) dx = csub(u[ry][rx + 1], u0);
+      if (gy <= a.ny - 2) dy = csub(u[ry + 1][rx], u0);
+      if (a.dims == 3 && q <= a.nz - 2) dz = csub(un[ry][rx], u0);
+      float2 qx = make_float2(0.f, 0.f), qy = qx, qz = qx;
+      if (!FIRST) {
+        qx = ring.slot(q, 1)[ry + 1][rx + 1];
+        qy = ring.slot(q, 2)[ry + 1][rx + 1];
+        if (a.dims == 3) qz = ring.slot(q, 3)[ry + 1][rx + 1];
+      }
+      qx = fma2(qx, a.step, dx);
+      qy = fma2(qy, a.step, dy);
+      qz = fma2(qz, a.step, dz);
+      project(qx, qy, qz);
+      p1[0][ry][rx] = qx;
+      p1[1][ry][rx] = qy;
+      p1[2][ry][rx] = qz;
+    }
+  };
+  // (c) u^1(q) over R1 (R1 origin is R2 (1, 1) and box (2, 2))
+  auto step_c = [&](int q) {
+    float2(*p1)[R2Y][R2X] = P1[q & 1];
+    float2(*p1m)[R2Y][R2X] = P1[(q + 1) & 1];   // plane q-1
+    float2(*vs)[BW] = ring.slot(q, 0);
+    float2(*u)[R1X] = U1[q & 1];
+    for (int e = tid; e < R1Y * R1X; e += kTvThreads) {
+      const int ry = e / R1X, rx = e - ry * R1X;
+      const int gx = i0 + rx, gy = j0 + ry;
+      float2 dh = make_float2(0.f, 0.f);
+      if (gx >= 1) dh = cadd(dh, p1[0][ry + 1][rx]);
+      if (gx <= a.nx - 2) dh = csub(dh, p1[0][ry + 1][rx + 1]);
+      if (gy >= 1) dh = cadd(dh, p1[1][ry][rx + 1]);
+      if (gy <= a.ny - 2) dh = csub(dh, p1[1][ry + 1][rx + 1]);
+      if (a.dims == 3) {
+        if (q >= 1) dh = cadd(dh, p1m[2][ry + 1][rx + 1]);
+        if (q <= a.nz - 2) dh = csub(dh, p1[2][ry + 1][rx + 1]);
+      }
+      const float2 v = vs[ry + 2][rx + 2];
+      u[ry][rx] = make_float2(v.x - a.mu * dh.x, v.y - a.mu * dh.y);
+    }
+  };
+  // (d) p^2(q) over the tile -> global
+  auto step_d = [&](int q) {
+    const int tx = tid % TX, ty = tid / TX;
+    const int gi = i0 + tx, gj = j0 + ty;
+    if (gi >= a.nx || gj >= a.ny) return;
+    float2(*u)[R1X] = U1[q & 1];
+    float2(*un)[R1X] = U1[(q + 1) & 1];
+    float2(*p1)[R2Y][R2X] = P1[q & 1];
+    const float2 u0 = u[ty][tx];
+    float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
+    if (gi <= a.nx - 2) dx = csub(u[ty][tx + 1], u0);
+    if (gj <= a.ny - 2) dy = csub(u[ty + 1][tx], u0);
+    if (a.dims == 3 && q <= a.nz - 2) dz = csub(un[ty][tx], u0);
+    float2 qx = fma2(p1[0][ty + 1][tx + 1], a.step, dx);
+    float2 qy = fma2(p1[1][ty + 1][tx + 1], a.step, dy);
+    float2 qz = fma2(p1[2][ty + 1][tx + 1], a.step, dz);
+    project(qx, qy, qz);
+    const size_t gidx = (static_cast<size_t>(q) * a.ny + gj) * a.nx + gi;
+    a.pout[0][gidx] = qx;
+    a.pout[1][gidx] = qy;
+    if (a.dims == 3) a.pout[2][gidx] = qz;
+  };
+
+  // pre-tick: u^0(zc0-1) needs planes zc0-2 (p_z) and zc0-1
+  if (!ring_wait(ring, zc0 - 2)) { ring_abort(ring, a, waited, issued); return; }
+  waited = zc0 - 2;
+  if (!ring_wait(ring, zc0 - 1)) { ring_abort(ring, a, waited, issued); return; }
+  waited = zc0 - 1;
+  step_a(zc0 - 1);
+  __syncthreads();
+
+  for (int t = zc0 - 1; t <= zc1; ++t) {
+    // stage of plane t-1 is free from tick t on: refill it with plane t+3
+    if (t + 3 <= qlast) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ring_issue<FIRST>(ring, a, t + 3, i0, j0);
+      }
+      issued = t + 3;
+    }
+    if (!ring_wait(ring, t + 1)) { ring_abort(ring, a, waited, issued); return; }
+    waited = t + 1;
+    step_a(t + 1);
+    __syncthreads();
+    step_b(t);
+    __syncthreads();
+    if (t >= zc0) {
+      step_c(t);
+      __syncthreads();
+      if (t >= zc0 + 1) step_d(t - 1);
+      __syncthreads();
+    }
   }
 }
 
@@ -427,13 +612,14 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
-cudaError_t launch_tv_step(bool first, const TvArgs& a, cudaStream_t s) {
+cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s) {
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
-  auto kern = first ? k_tv_step<true> : k_tv_step<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TvLayout::kBytes);
+  auto kern = nsteps == 2 ? (first ? k_tv_step2<true> : k_tv_step2<false>)
+                          : (first ? k_tv_step<true> : k_tv_step<false>);
+  const int bytes = nsteps == 2 ? TvLayout2::kBytes : TvLayout1::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kTvThreads, TvLayout::kBytes, s>>>(a);
+  kern<<<grid, kTvThreads, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
