@@ -288,8 +288,11 @@ def main():
 
     # roofline of the TV dual step, from the live stage events
     tv_ms, tv_launches = stages["tv"]
-    per_prox = w.n_inner
-    alg_bytes_per_launch = w.nvox * (32 + 56 * (per_prox - 1)) / per_prox
+    # 32 B/voxel for the launch that starts from p = 0 (reads v, writes p),
+    # 56 B/voxel for every other launch (reads v and p, writes p), whatever
+    # number of dual steps a launch performs.
+    per_prox = tv_launches // (args.steps * (w.iters + 0)) if tv_launches else 1
+    alg_bytes_per_launch = w.nvox * (32 + 56 * (per_prox - 1)) / max(per_prox, 1)
     avg_launch_s = (tv_ms / 1e3) / max(tv_launches, 1)
     achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if tv_launches else None
     peak, peak_kind = hbm_peak()

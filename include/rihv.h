@@ -56,7 +56,8 @@ typedef enum {
 } rihv_status;
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
- * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0. */
+ * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
+ * tv_steps_per_launch 1. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -66,6 +67,9 @@ typedef struct {
   int check_every;   /* evaluate F(x_k) every M iterations (0: never)        */
   double tol;        /* with f_star > 0: stop at the first check where       */
   double f_star;     /*   F(x_k) <= f_star * (1 + tol)                       */
+  int tv_steps_per_launch; /* 1: one dual step per kernel launch; 2: two
+                        steps per launch (same arithmetic, scheduled with
+                        the first step recomputed on a shared-memory halo)   */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */

@@ -263,8 +263,10 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
 
 // K dual steps; returns the buffer set holding the final p.
 rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
-  // Two dual steps per launch; a single-step launch finishes an odd count.
-  const int launches = k / 2 + (k % 2);
+  // With tv_steps_per_launch = 2, two dual steps per launch and a single-step
+  // launch for an odd remainder.
+  const int per = h->opt.tv_steps_per_launch;
+  const int launches = per == 2 ? k / 2 + (k % 2) : k;
   StageScope sc(h, ST_TV, launches);
   TvArgs a{};
   CK(make_volume_tmap(&a.tm_v, v, h->nx, h->ny, h->nz));
@@ -282,7 +284,7 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   const CUtensorMap* tdst = h->tm_pa;
   int done = 0;
   while (done < k) {
-    const int n = (k - done >= 2) ? 2 : 1;
+    const int n = (per == 2 && k - done >= 2) ? 2 : 1;
     for (int c = 0; c < 3; ++c) {
       a.tm_p[c] = tsrc[c];
       a.pout[c] = dst[c];
@@ -343,6 +345,7 @@ void rihv_default_options(rihv_options* o) {
   o->check_every = 10;
   o->tol = 0.0;
   o->f_star = 0.0;
+  o->tv_steps_per_launch = 1;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -494,7 +497,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
   if (!h || !o) return fail(h, RIHV_ERR_INVALID_ARG, "null argument");
   if ((o->tv_dims != 2 && o->tv_dims != 3) || o->n_inner < 0 || o->check_every < 0 ||
       o->tol < 0 || o->f_star < 0 || (o->restart != 0 && o->restart != 1) ||
-      (o->accelerate != 0 && o->accelerate != 1))
+      (o->accelerate != 0 && o->accelerate != 1) ||
+      (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   h->opt = *o;
   return RIHV_OK;

@@ -93,14 +93,15 @@ def test_adjoint_identity_on_gpu():
     assert abs(lhs - rhs) / (np.linalg.norm(hx) * np.linalg.norm(r)) < 1e-6
 
 
+@pytest.mark.parametrize("per_launch", [1, 2])
 @pytest.mark.parametrize("dims", [3, 2])
 @pytest.mark.parametrize("nx,ny,nz,k", [(48, 24, 37, 20), (24, 16, 5, 1), (64, 32, 33, 7),
                                          (16, 16, 1, 5)])
-def test_prox_parity(nx, ny, nz, k, dims):
+def test_prox_parity(nx, ny, nz, k, dims, per_launch):
     op = optics(nx, ny, nz)
     v = synth.random_complex(synth.Stream(nz * 3 + k), op.shape)
     h = handle(op)
-    h.set_options(tv_dims=dims)
+    h.set_options(tv_dims=dims, tv_steps_per_launch=per_launch)
     out = torch.empty(op.shape, dtype=torch.complex64, device=dev())
     t_l1, t_tv = 0.3, 0.05
     h.prox_fused_lasso(to_dev(v), t_l1, t_tv, k, out)
