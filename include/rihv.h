@@ -148,6 +148,34 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
                         rihv_particle* out, int max_out, int* n_out);
 
+/* Fused-lasso prox without any allocation. The paper has no counterpart to
+ * this entry point; it exists for callers that cannot call cudaMalloc, such
+ * as code running while a CUDA graph is captured, hosts that hand out device
+ * memory only from their own fixed arena, and services that stop allocating
+ * after start-up so that no request fails for lack of memory.
+ *
+ * It computes exactly what rihv_prox_fused_lasso computes (tv_dims TV prox by
+ * inner_iters dual gradient-projection steps from p = 0, then soft threshold
+ * with t_l1), without a handle. Its scratch (the dual variable) is a static
+ * device array inside the library of 6 x 8 MiB + 256 B, reserved on every GPU
+ * that loads the library until the process exits. Limits: nx even and >= 2,
+ * ny, nz >= 1, nx*ny*nz <= 1,048,576 voxels; larger volumes return
+ * RIHV_ERR_UNSUPPORTED_SIZE before any work is queued.
+ *
+ * v, x_out: distinct device complex64 [nz][ny][nx], 16-byte aligned (else
+ * RIHV_ERR_INVALID_ARG). stream: a cudaStream_t or NULL. The work is queued on
+ * the stream and the call returns; it calls no cudaMalloc, cudaFree or other
+ * allocating routine. The first call on each device looks up the scratch's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. All calls share the one scratch array,
+ * which keeps the last call's contents: calls that may overlap on the GPU
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller. A bounded-wait failure inside the TV kernels only sets a flag
+ * in that scratch and is not reported by this call. */
+rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out, int nx, int ny, int nz,
+                                          int tv_dims, float t_l1, float t_tv, int inner_iters,
+                                          void* stream);
+
 /* Per-stage timing. Kernel launches are always counted per stage. When
  * profiling is on, the library also records CUDA events around its stages on
  * the handle's stream. rihv_stage_times returns accumulated milliseconds (0

@@ -229,3 +229,24 @@ class Rihv:
     prox_fused_lasso = rihv_prox_fused_lasso
     solve = rihv_solve
     detect = rihv_detect
+
+
+def rihv_prox_fused_lasso_noalloc(v, x_out, nz, ny, nx, tv_dims, t_l1, t_tv, inner_iters,
+                                  stream=None):
+    """The fused-lasso prox without any device allocation (static scratch in the
+    library; see include/rihv.h). For callers that cannot allocate, e.g. inside
+    a CUDA graph capture or under a fixed memory arena. Volumes up to 1,048,576
+    voxels; nx must be even. Calls that overlap on the GPU share the scratch and
+    race."""
+    L = load_library()
+    fn = L.rihv_prox_fused_lasso_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_void_p]
+    n = int(nx) * int(ny) * int(nz)
+    st = fn(_ptr(v, device=True, dtype="complex64", numel=n, name="v"),
+            _ptr(x_out, device=True, dtype="complex64", numel=n, name="x_out"),
+            int(nx), int(ny), int(nz), int(tv_dims), float(t_l1), float(t_tv), int(inner_iters),
+            getattr(stream, "cuda_stream", stream))
+    if st != 0:
+        raise RihvError(st, "rihv_prox_fused_lasso_noalloc failed")
