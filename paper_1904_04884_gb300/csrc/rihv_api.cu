@@ -95,7 +95,7 @@ struct rihv_ctx {
   int trace_cap = 0;
   int* det_err = nullptr;
   int* tv_err = nullptr;       // set by a TV kernel whose bounded wait gave up
-  CUtensorMap tm_pa[3], tm_pb[3];
+  CUtensorMap tm_pa[2][3], tm_pb[2][3];   // [one-step box, two-step box]
   DetectWork det{};
   std::vector<void*> allocs;
 
@@ -268,8 +268,10 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   const int per = h->opt.tv_steps_per_launch;
   const int launches = per == 2 ? k / 2 + (k % 2) : k;
   StageScope sc(h, ST_TV, launches);
+  CUtensorMap tm_v[2];
+  CK(make_volume_tmap(&tm_v[0], v, h->nx, h->ny, h->nz, kTvBoxH1));
+  if (per == 2) CK(make_volume_tmap(&tm_v[1], v, h->nx, h->ny, h->nz, kTvBoxH2));
   TvArgs a{};
-  CK(make_volume_tmap(&a.tm_v, v, h->nx, h->ny, h->nz));
   a.err = h->tv_err;
   a.nx = h->nx;
   a.ny = h->ny;
@@ -280,19 +282,20 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   a.step = 1.f / (4.f * a.dims * mu);
   float2** src = h->pb;
   float2** dst = h->pa;
-  const CUtensorMap* tsrc = h->tm_pb;
-  const CUtensorMap* tdst = h->tm_pa;
+  bool src_is_b = true;
   int done = 0;
   while (done < k) {
     const int n = (per == 2 && k - done >= 2) ? 2 : 1;
+    const int b = n == 2 ? 1 : 0;
+    a.tm_v = tm_v[b];
     for (int c = 0; c < 3; ++c) {
-      a.tm_p[c] = tsrc[c];
+      a.tm_p[c] = src_is_b ? h->tm_pb[b][c] : h->tm_pa[b][c];
       a.pout[c] = dst[c];
     }
     CK(launch_tv_step(done == 0, n, a, h->stream));
     done += n;
     std::swap(src, dst);
-    std::swap(tsrc, tdst);
+    src_is_b = !src_is_b;
   }
   *pfinal = src;
   return RIHV_OK;
@@ -416,11 +419,13 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
       cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(h->tv_err, 0, sizeof(int)) != cudaSuccess)
     return cleanup(fail(h, RIHV_ERR_CUDA, "memset failed"));
-  for (int c = 0; c < 3; ++c) {
-    if (make_volume_tmap(&h->tm_pa[c], h->pa[c], nx, ny, nz) != cudaSuccess ||
-        make_volume_tmap(&h->tm_pb[c], h->pb[c], nx, ny, nz) != cudaSuccess)
-      return cleanup(fail(h, RIHV_ERR_CUDA, "tensor map encoding failed"));
-  }
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < 3; ++c) {
+      const int rows = b == 0 ? kTvBoxH1 : kTvBoxH2;
+      if (make_volume_tmap(&h->tm_pa[b][c], h->pa[c], nx, ny, nz, rows) != cudaSuccess ||
+          make_volume_tmap(&h->tm_pb[b][c], h->pb[c], nx, ny, nz, rows) != cudaSuccess)
+        return cleanup(fail(h, RIHV_ERR_CUDA, "tensor map encoding failed"));
+    }
 
   // Twiddles exp(-2 pi i m / n) in FP64, rounded to float.
   auto twiddles = [](int n) {

@@ -23,10 +23,10 @@ constexpr int kMaxPasses = 8;
 constexpr int kTvTx = 32;          // TV tile width (x)
 constexpr int kTvTy = 8;           // TV tile height (y)
 constexpr int kTvThreads = kTvTx * kTvTy;
-constexpr int kTvBoxW = kTvTx + 4; // TMA box width in complex elements (x from i0-2)
-constexpr int kTvBoxH = kTvTy + 4; // TMA box height (y from j0-2)
-constexpr int kTvStages = 4;       // planes in the shared-memory ring
-constexpr int kTvSlotBytes = ((kTvBoxW * kTvBoxH * 8 + 127) / 128) * 128;
+constexpr int kTvBoxW = kTvTx + 4;  // TMA box width in complex elements (x from i0-2)
+constexpr int kTvBoxH1 = kTvTy + 2; // box height, one step per launch (y from j0-1)
+constexpr int kTvBoxH2 = kTvTy + 4; // box height, two steps per launch (y from j0-2)
+constexpr int kTvStages = 4;        // planes in the shared-memory ring
 
 constexpr int kRedBlocks = 1216;   // fixed grid of the streaming reduction kernels (8 x 152)
 constexpr int kRedThreads = 256;
@@ -103,7 +103,7 @@ cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, f
 // TV / prox / FISTA kernels (tv_kernels.cu)
 // ---------------------------------------------------------------------------
 struct TvArgs {
-  CUtensorMap tm_v;    // v (see make_volume_tmap)
+  CUtensorMap tm_v;    // v (see make_volume_tmap; box height per schedule)
   CUtensorMap tm_p[3]; // dual input p_x, p_y, p_z
   float2* pout[3];     // dual output (must not alias the input)
   int* err;            // set to 1 if a bounded wait gave up
@@ -114,7 +114,9 @@ struct TvArgs {
 };
 // nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero.
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s);
-cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz);
+// box_rows: kTvBoxH1 for the one-step kernel, kTvBoxH2 for the two-step one.
+cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
+                             int box_rows);
 
 enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };
 struct FinArgs {

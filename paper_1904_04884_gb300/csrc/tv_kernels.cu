@@ -10,9 +10,9 @@
 //
 // The TV kernels march a 32x8 x-y tile through a chunk of planes (2.5D
 // blocking). Each plane of v, p_x, p_y, p_z arrives in shared memory as one
-// TMA box (x from i0-2, y from j0-2: the stencil's halo, with the x start kept
-// on a 16-byte boundary; out-of-range boxes are zero filled) into a 4-stage
-// ring completed by mbarriers, so two planes are in flight while one is
+// TMA box (x from i0-2, y from j0-1 for one step or j0-2 for two: the
+// stencil's halo, with the x start kept on a 16-byte boundary; out-of-range
+// boxes are zero filled) into a 4-stage ring completed by mbarriers, so two planes are in flight while one is
 // computed. k_tv_step2 performs two dual steps per launch (temporal blocking,
 // first step recomputed on a halo ring in shared memory); k_tv_step performs
 // one (for odd step counts). Outputs go out with plain coalesced stores. Every
@@ -37,9 +37,12 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 constexpr int TX = kTvTx;
 constexpr int TY = kTvTy;
 constexpr int BW = kTvBoxW;       // TMA box: complex x in [i0-2, i0+TX+2)
-constexpr int BH = kTvBoxH;       //          y in [j0-2, j0+TY+2)
+constexpr int BH1 = kTvBoxH1;     //   one step:  y in [j0-1, j0+TY+1)
+constexpr int BH2 = kTvBoxH2;     //   two steps: y in [j0-2, j0+TY+2)
 constexpr int NSTAGE = kTvStages;
-constexpr int SLOT = kTvSlotBytes;
+constexpr int slot_bytes(int bh) { return ((BW * bh * 8 + 127) / 128) * 128; }
+constexpr int SLOT1 = slot_bytes(BH1);
+constexpr int SLOT2 = slot_bytes(BH2);
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
 
 // Regions (x extent, y extent) relative to the tile origin (i0, j0):
@@ -100,27 +103,31 @@ __device__ __forceinline__ void project(float2& qx, float2& qy, float2& qz) {
   }
 }
 
-// Plane ring fed by TMA: NSTAGE stages x 4 slots (v, p_x, p_y, p_z). Plane q
-// lives in stage (q - base) mod NSTAGE; its n-th use has mbarrier parity n&1.
+// Plane ring fed by TMA: NSTAGE stages x 4 slots (v, p_x, p_y, p_z) of a
+// BH-row box each. Plane q lives in stage (q - base) mod NSTAGE; its n-th use
+// has mbarrier parity n&1.
+template <int BH>
 struct PlaneRing {
+  static constexpr int kSlot = slot_bytes(BH);
+  static constexpr int kY0 = (BH - TY) / 2;   // box row of the tile's first row
   unsigned char* smem;
   unsigned long long* bars;
   int base;
   __device__ float2 (*slot(int q, int arr) const)[BW] {
     const int s = (q - base) & (NSTAGE - 1);
-    return reinterpret_cast<float2(*)[BW]>(smem + (s * 4 + arr) * SLOT);
+    return reinterpret_cast<float2(*)[BW]>(smem + (s * 4 + arr) * kSlot);
   }
   __device__ unsigned bar(int q) const { return smem_addr(&bars[(q - base) & (NSTAGE - 1)]); }
   __device__ unsigned parity(int q) const { return static_cast<unsigned>(((q - base) / NSTAGE) & 1); }
 };
 
-template <bool FIRST>
-__device__ __forceinline__ void ring_issue(const PlaneRing& r, const TvArgs& a, int q, int i0,
+template <bool FIRST, int BH>
+__device__ __forceinline__ void ring_issue(const PlaneRing<BH>& r, const TvArgs& a, int q, int i0,
                                            int j0) {
   const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
   const unsigned bar = r.bar(q);
   mbar_expect_tx(bar, static_cast<unsigned>(nslots * BW * BH * 8));
-  const int x = 2 * (i0 - 2), y = j0 - 2;
+  const int x = 2 * (i0 - 2), y = j0 - PlaneRing<BH>::kY0;
   tma_load_3d(smem_addr(r.slot(q, 0)), &a.tm_v, x, y, q, bar);
   if (!FIRST) {
     tma_load_3d(smem_addr(r.slot(q, 1)), &a.tm_p[0], x, y, q, bar);
@@ -130,14 +137,16 @@ __device__ __forceinline__ void ring_issue(const PlaneRing& r, const TvArgs& a, 
 }
 
 // Block-uniform bounded wait for plane q.
-__device__ __forceinline__ bool ring_wait(const PlaneRing& r, int q) {
+template <int BH>
+__device__ __forceinline__ bool ring_wait(const PlaneRing<BH>& r, int q) {
   const bool ok = mbar_wait(r.bar(q), r.parity(q));
   return __syncthreads_and(ok) != 0;
 }
 
 // Records a failed wait and drains this CTA's copies in flight (bounded)
 // before its shared memory is released.
-__device__ __forceinline__ void ring_abort(const PlaneRing& r, const TvArgs& a, int waited,
+template <int BH>
+__device__ __forceinline__ void ring_abort(const PlaneRing<BH>& r, const TvArgs& a, int waited,
                                            int issued) {
   if (threadIdx.x == 0) {
     atomicExch(a.err, 1);
@@ -171,7 +180,7 @@ __device__ __forceinline__ float2 u_from_box(const TvArgs& a, float2 (*vs)[BW], 
 
 struct TvLayout1 {   // one dual step per launch
   static constexpr int kUBytes = 2 * R1Y * R1X * 8;
-  static constexpr int kBarOffset = NSTAGE * 4 * SLOT + kUBytes;
+  static constexpr int kBarOffset = NSTAGE * 4 * SLOT1 + kUBytes;
   static constexpr int kBytes = kBarOffset + NSTAGE * 8;
 };
 
@@ -179,9 +188,9 @@ struct TvLayout1 {   // one dual step per launch
 template <bool FIRST>
 __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ TvArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float2(*U)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + NSTAGE * 4 * SLOT);
-  PlaneRing ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout1::kBarOffset),
-                 static_cast<int>(blockIdx.z) * a.zchunk - 1};
+  float2(*U)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + NSTAGE * 4 * SLOT1);
+  PlaneRing<BH1> ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout1::kBarOffset),
+                      static_cast<int>(blockIdx.z) * a.zchunk - 1};
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
@@ -205,7 +214,7 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
     for (int e = tid; e < R1Y * R1X; e += kTvThreads) {
       const int ry = e / R1X, rx = e - ry * R1X;
       u[ry][rx] = u_from_box<FIRST>(a, ring.slot(k, 0), ring.slot(k, 1), ring.slot(k, 2),
-                                    ring.slot(k, 3), ring.slot(k - 1, 3), ry + 2, rx + 2, i0 + rx,
+                                    ring.slot(k, 3), ring.slot(k - 1, 3), ry + 1, rx + 2, i0 + rx,
                                     j0 + ry, k);
     }
   };
@@ -242,9 +251,9 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
       if (a.dims == 3 && k <= a.nz - 2) gz = csub(un[ty][tx], u0);
       float2 qx = make_float2(0.f, 0.f), qy = qx, qz = qx;
       if (!FIRST) {
-        qx = ring.slot(k, 1)[ty + 2][tx + 2];
-        qy = ring.slot(k, 2)[ty + 2][tx + 2];
-        if (a.dims == 3) qz = ring.slot(k, 3)[ty + 2][tx + 2];
+        qx = ring.slot(k, 1)[ty + 1][tx + 2];
+        qy = ring.slot(k, 2)[ty + 1][tx + 2];
+        if (a.dims == 3) qz = ring.slot(k, 3)[ty + 1][tx + 2];
       }
       qx = fma2(qx, a.step, gx);
       qy = fma2(qy, a.step, gy);
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
 }
 
 struct TvLayout2 {   // two dual steps per launch
-  static constexpr int kU0Off = NSTAGE * 4 * SLOT;
+  static constexpr int kU0Off = NSTAGE * 4 * SLOT2;
   static constexpr int kU0Bytes = 2 * AY * AX * 8;
   static constexpr int kP1Off = kU0Off + kU0Bytes;
   static constexpr int kP1Bytes = 2 * 3 * R2Y * R2X * 8;
@@ -289,7 +298,8 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_step2(const __grid_constan
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
   // planes zc0-2 .. zc1+1 are read (out-of-range planes arrive zero filled)
-  PlaneRing ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset), zc0 - 2};
+  PlaneRing<BH2> ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset),
+                      zc0 - 2};
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tid = threadIdx.x;
   const int qlast = zc1 + 1;
@@ -624,8 +634,9 @@ cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t
 }
 
 // 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box
-// of kTvBoxH rows x 2 kTvBoxW floats x 1 plane, zero fill out of bounds.
-cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz) {
+// of box_rows rows x 2 kTvBoxW floats x 1 plane, zero fill out of bounds.
+cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
+                             int box_rows) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -643,7 +654,7 @@ cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, 
                               static_cast<cuuint64_t>(nz)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(8) * nx,
                                  static_cast<cuuint64_t>(8) * nx * ny};
-  const cuuint32_t box[3] = {2 * kTvBoxW, kTvBoxH, 1};
+  const cuuint32_t box[3] = {2 * kTvBoxW, static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
