@@ -69,6 +69,7 @@ struct rihv_ctx {
   rihv_options opt{};
   int device = 0;
   int groups = 1, zpg = 1;
+  int sms = 152;
   int tv_zchunk = 32;
   double tau = 0;
   FftPlan plan_x{}, plan_y{};
@@ -327,6 +328,27 @@ rihv_status prox_into(rihv_ctx* h, const float2* v, float t_l1, float t_tv, int 
   return RIHV_OK;
 }
 
+constexpr int kMaxGroups = 32;
+
+void choose_groups(rihv_ctx* h, int nz) {
+  const int strips = h->nx / kStrip;
+  const double slots = 2.0 * h->sms;
+  int best_zpg = nz;
+  double best_eff = -1.0;
+  for (int zpg = nz; zpg >= 1; --zpg) {
+    const int g = (nz + zpg - 1) / zpg;
+    if (g > kMaxGroups) break;
+    const double waves = strips * g / slots;
+    const double eff = waves < 1.0 ? waves : waves / std::ceil(waves);
+    if (eff > best_eff + 0.03) {
+      best_eff = eff;
+      best_zpg = zpg;
+    }
+  }
+  h->zpg = best_zpg;
+  h->groups = (nz + best_zpg - 1) / best_zpg;
+}
+
 rihv_status copy_in(rihv_ctx* h, void* dst, const void* src, size_t bytes) {
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
   return RIHV_OK;
@@ -377,14 +399,12 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   h->plan_y = make_plan(ny);
   cudaGetDevice(&h->device);
 
-  // z-groups of the column passes: about 4 CTAs per SM in total.
+  // z-groups of the column passes: the fewest groups whose grid fills whole
+  // waves of the resident slots (2 CTAs per SM) to within 3 %, at most 32.
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  const int strips = nx / kStrip;
-  int g = (4 * sms + strips - 1) / strips;
-  g = std::max(1, std::min(g, nz));
-  h->zpg = (nz + g - 1) / g;
-  h->groups = (nz + h->zpg - 1) / h->zpg;
+  h->sms = sms;
+  choose_groups(h, nz);
 
   auto cleanup = [&](rihv_status st) {
     rihv_destroy(h);
@@ -398,7 +418,7 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   AL(h->phase, h->nxy);
   AL(h->amp, h->nxy);
   AL(h->inter, h->nvox);
-  AL(h->partial, h->nxy * h->groups);
+  AL(h->partial, h->nxy * kMaxGroups);
   AL(h->spec, h->nxy);
   AL(h->bhat, h->nxy);
   AL(h->holo, h->nxy);
