@@ -115,13 +115,15 @@ struct Dft<3, INV> {
 };
 
 // Tile layout for B = 4 interleaved transforms of length n: element (n, b)
-// at row'(n) * 4 + b, rows permuted inside aligned blocks of four,
-// row'(n) = (n & ~3) | ((n + n/8) & 3). Eight consecutive rows, and eight rows
-// at a stride of 2, 4 or 8 (the first Stockham pass), then fall into distinct
-// 32-byte bank groups, so every warp access of a pass takes the minimum two
+// at row'(n) * 4 + (b ^ ((n / 8) mod 4)), rows permuted inside aligned blocks
+// of four, row'(n) = (n & ~3) | ((n + n/8) & 3). Eight consecutive rows, and
+// eight rows at a stride of 2, 4 or 8 (the first Stockham pass), fall into
+// distinct 32-byte bank groups; the XOR spreads 32 consecutive rows of one
+// transform (a row-contiguous global access) over all banks. Every warp access
+// of the engine and of the loads and stores takes the minimum two
 // shared-memory wavefronts. No padding.
 __device__ __forceinline__ int tix(int n, int b) {
-  return (((n & ~3) | ((n + (n >> 3)) & 3)) << 2) | b;
+  return (((n & ~3) | ((n + (n >> 3)) & 3)) << 2) | (b ^ ((n >> 3) & 3));
 }
 
 // One out-of-place Stockham pass of radix R over the four interleaved
@@ -201,20 +203,21 @@ __device__ __forceinline__ float2 row_load(const RowArgs& a, int item, int e, in
     const int s = e / (B * W), w = e - s * (B * W);
     return static_cast<const float2*>(a.src)[((z * (a.nx / W) + s) * a.ny + r0) * W + w];
   }
-  const int rl = e & 3, col = e >> 2;
+  const int rl = e / a.nx, col = e - rl * a.nx;    // a warp reads 256 contiguous bytes
   const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
   if (IN == ROW_IN_F32) return make_float2(static_cast<const float*>(a.src)[gi], 0.f);
   return static_cast<const float2*>(a.src)[gi];
 }
 
 template <int IN>
-__device__ __forceinline__ int row_tile_index(int e) {
+__device__ __forceinline__ int row_tile_index(int e, int nx) {
   constexpr int B = kRowsPerCta, W = kStrip;
   if (IN == ROW_IN_STRIP) {
     const int s = e / (B * W), w = e - s * (B * W);
     return tix(s * W + (w & 3), w >> 2);
   }
-  return tix(e >> 2, e & 3);
+  const int rl = e / nx;
+  return tix(e - rl * nx, rl);
 }
 
 template <bool INV, int IN, int OUT, int EPI>
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__
 #pragma unroll
     for (int q = 0; q < kRowMaxE; ++q) {
       const int e = threadIdx.x + q * T;
-      if (e < total) tile[row_tile_index<IN>(e)] = pre[q];
+      if (e < total) tile[row_tile_index<IN>(e, n)] = pre[q];
     }
     __syncthreads();
     const int next = item + gridDim.x;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__
         a.dst[((z * (a.nx / W) + s) * a.ny + r0) * W + w] =
             cscale(res[tix(s * W + (w & 3), w >> 2)], a.scale);
       } else {
-        const int rl = e & 3, col = e >> 2;
+        const int rl = e / n, col = e - rl * n;
         const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
         const float2 g = res[tix(col, rl)];
         if (EPI == ROW_EPI_GRAD) {
