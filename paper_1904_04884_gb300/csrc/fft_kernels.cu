@@ -3,14 +3,12 @@
 //
 // Design (GB300): a 2D transform of an n_y x n_x plane is a row pass (length
 // n_x transforms along x) and a column pass (length n_y along y). Both passes
-// run the same shared-memory Stockham engine on a tile of four independent
-// transforms stored interleaved (see tix: a row permutation that keeps every
-// warp access at two wavefronts), so that lanes of a warp that work on the
-// same butterfly index touch consecutive words. Radix 2/3/4/8 butterflies run
-// in registers, out of place between two tiles; twiddles exp(-2 pi i m / n)
-// come from an FP64-computed table staged in shared memory. Each CTA fetches
-// the next plane (column pass) or the next four rows (row pass) into
-// registers while it transforms the current one.
+// run the same shared-memory Stockham engine on a tile of B independent
+// transforms stored interleaved, tile[n * (B + 1) + b], so that lanes of a
+// warp that work on the same butterfly index touch consecutive words. Radix
+// 2/3/4/8 butterflies run in registers, out of place between two tiles;
+// twiddles exp(-2 pi i m / n) come from an FP64-computed table staged in
+// shared memory. Two CTAs of 512 threads fit on an SM at n = 1024.
 //
 // Between the passes, planes live in a strip-major intermediate layout
 // [z][n_x / W][n_y][W] (W = kStrip) so that one column strip of one plane is a
@@ -114,35 +112,24 @@ struct Dft<3, INV> {
   }
 };
 
-// Tile layout for B = 4 interleaved transforms of length n: element (n, b)
-// at row'(n) * 4 + (b ^ ((n / 8) mod 4)), rows permuted inside aligned blocks
-// of four, row'(n) = (n & ~3) | ((n + n/8) & 3). Eight consecutive rows, and
-// eight rows at a stride of 2, 4 or 8 (the first Stockham pass), fall into
-// distinct 32-byte bank groups; the XOR spreads 32 consecutive rows of one
-// transform (a row-contiguous global access) over all banks. Every warp access
-// of the engine and of the loads and stores takes the minimum two
-// shared-memory wavefronts. No padding.
-__device__ __forceinline__ int tix(int n, int b) {
-  return (((n & ~3) | ((n + (n >> 3)) & 3)) << 2) | (b ^ ((n >> 3) & 3));
-}
-
-// One out-of-place Stockham pass of radix R over the four interleaved
-// transforms of length n. Butterfly i (k = i mod p, p = product of the radices
-// of earlier passes) reads x[i + j n/R], multiplies input j by w^(j k),
-// w = exp(-+2 pi i/(p R)), transforms, and writes output m to position
-// (i - k) R + k + m p. Threads take butterflies in turn (transform index
-// fastest), each holding only its R values.
-template <int R, bool INV>
+// One out-of-place Stockham pass of radix R over B interleaved transforms of
+// length n (tile[n * (B + 1) + b]). Butterfly i (k = i mod p, p = product of
+// the radices of earlier passes) reads x[i + j n/R], multiplies input j by
+// w^(j k), w = exp(-+2 pi i/(p R)), transforms, and writes output m to
+// position (i - k) R + k + m p. Threads take butterflies in turn, each holding
+// only its R values, which keeps the register footprint small.
+template <int R, int B, bool INV>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* __restrict__ out,
                                          int n, int p, const float2* __restrict__ tw) {
+  constexpr int LD = B + 1;
   const int nr = n / R;
-  const int nbf = nr * 4;
+  const int nbf = nr * B;
   const int tstride = n / (p * R);
   for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-    const int b = bf & 3, i = bf >> 2;
+    const int b = bf % B, i = bf / B;
     float2 v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = in[tix(i + j * nr, b)];
+    for (int j = 0; j < R; ++j) v[j] = in[(i + j * nr) * LD + b];
     const int k = i % p;
     if (p > 1) {
 #pragma unroll
@@ -154,27 +141,27 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* 
     Dft<R, INV>::run(v);
     const int base = (i - k) * R + k;
 #pragma unroll
-    for (int m = 0; m < R; ++m) out[tix(base + m * p, b)] = v[m];
+    for (int m = 0; m < R; ++m) out[(base + m * p) * LD + b] = v[m];
   }
   __syncthreads();
 }
 
 // Runs all passes of the plan, ping-ponging between two tiles; returns the
 // tile holding the result.
-template <bool INV>
+template <int B, bool INV>
 __device__ __forceinline__ float2* fft_run(float2* t0, float2* t1, const FftPlan& plan,
                                            const float2* tw) {
   int p = 1;
   for (int s = 0; s < plan.npass; ++s) {
     const int r = plan.radix[s];
     if (r == 8)
-      fft_pass<8, INV>(t0, t1, plan.n, p, tw);
+      fft_pass<8, B, INV>(t0, t1, plan.n, p, tw);
     else if (r == 4)
-      fft_pass<4, INV>(t0, t1, plan.n, p, tw);
+      fft_pass<4, B, INV>(t0, t1, plan.n, p, tw);
     else if (r == 2)
-      fft_pass<2, INV>(t0, t1, plan.n, p, tw);
+      fft_pass<2, B, INV>(t0, t1, plan.n, p, tw);
     else
-      fft_pass<3, INV>(t0, t1, plan.n, p, tw);
+      fft_pass<3, B, INV>(t0, t1, plan.n, p, tw);
     p *= r;
     float2* t = t0;
     t0 = t1;
@@ -188,91 +175,67 @@ __device__ __forceinline__ void stage_twiddles(float2* dst, const float2* src, i
 }
 
 // ---------------------------------------------------------------------------
-// Row pass: four rows of one plane per work item; transforms along x.
-// Persistent grid; each item's input is fetched into registers while the
-// previous item is transformed.
+// Row pass: kRowsPerCta rows of one plane; transforms along x.
+// grid (ny / kRowsPerCta, nz)
 // ---------------------------------------------------------------------------
-constexpr int kRowMaxE = kMaxN * kRowsPerCta / kFftThreads;   // elements per thread
-
-template <int IN>
-__device__ __forceinline__ float2 row_load(const RowArgs& a, int item, int e, int rblocks) {
-  constexpr int B = kRowsPerCta, W = kStrip;
-  const int r0 = (item % rblocks) * B;
-  const size_t z = item / rblocks;
-  if (IN == ROW_IN_STRIP) {
-    const int s = e / (B * W), w = e - s * (B * W);
-    return static_cast<const float2*>(a.src)[((z * (a.nx / W) + s) * a.ny + r0) * W + w];
-  }
-  const int rl = e / a.nx, col = e - rl * a.nx;    // a warp reads 256 contiguous bytes
-  const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
-  if (IN == ROW_IN_F32) return make_float2(static_cast<const float*>(a.src)[gi], 0.f);
-  return static_cast<const float2*>(a.src)[gi];
-}
-
-template <int IN>
-__device__ __forceinline__ int row_tile_index(int e, int nx) {
-  constexpr int B = kRowsPerCta, W = kStrip;
-  if (IN == ROW_IN_STRIP) {
-    const int s = e / (B * W), w = e - s * (B * W);
-    return tix(s * W + (w & 3), w >> 2);
-  }
-  const int rl = e / nx;
-  return tix(e - rl * nx, rl);
-}
-
 template <bool INV, int IN, int OUT, int EPI>
 __global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__ RowArgs a) {
   constexpr int B = kRowsPerCta;
+  constexpr int LD = B + 1;
   constexpr int T = kFftThreads;
   constexpr int W = kStrip;
   extern __shared__ float2 smem[];
   const int n = a.nx;
   float2* tile = smem;
-  float2* tile2 = smem + n * B;
-  float2* tw = smem + 2 * n * B;
+  float2* tile2 = smem + n * LD;
+  float2* tw = smem + 2 * n * LD;
   stage_twiddles(tw, a.tw, n);
 
+  const int nstrip = a.nx / W;
   const int total = B * n;
   const int rblocks = a.ny / B;
   const int nitems = rblocks * a.nz;
-  float2 pre[kRowMaxE];
-  int item = blockIdx.x;
-  if (item < nitems) {
-#pragma unroll
-    for (int q = 0; q < kRowMaxE; ++q) {
-      const int e = threadIdx.x + q * T;
-      if (e < total) pre[q] = row_load<IN>(a, item, e, rblocks);
-    }
-  }
-  for (; item < nitems; item += gridDim.x) {
+  __syncthreads();
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int r0 = (item % rblocks) * B;
     const size_t z = item / rblocks;
-#pragma unroll
-    for (int q = 0; q < kRowMaxE; ++q) {
-      const int e = threadIdx.x + q * T;
-      if (e < total) tile[row_tile_index<IN>(e, n)] = pre[q];
+
+    // Load B rows, transposed into the interleaved tile.
+    for (int e = threadIdx.x; e < total; e += T) {
+      int rl, col;
+      float2 val;
+      if (IN == ROW_IN_STRIP) {
+        const int s = e / (B * W), w = e - s * (B * W);
+        rl = w / W;
+        col = s * W + (w - rl * W);
+        const float2* src = static_cast<const float2*>(a.src);
+        val = src[((z * nstrip + s) * a.ny + r0) * W + w];
+      } else {
+        rl = e / n;
+        col = e - rl * n;
+        const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
+        if (IN == ROW_IN_F32)
+          val = make_float2(static_cast<const float*>(a.src)[gi], 0.f);
+        else
+          val = static_cast<const float2*>(a.src)[gi];
+      }
+      tile[col * LD + rl] = val;
     }
     __syncthreads();
-    const int next = item + gridDim.x;
-    if (next < nitems) {
-#pragma unroll
-      for (int q = 0; q < kRowMaxE; ++q) {
-        const int e = threadIdx.x + q * T;
-        if (e < total) pre[q] = row_load<IN>(a, next, e, rblocks);
-      }
-    }
 
-    const float2* res = fft_run<INV>(tile, tile2, a.plan, tw);
+    const float2* res = fft_run<B, INV>(tile, tile2, a.plan, tw);
 
     for (int e = threadIdx.x; e < total; e += T) {
       if (OUT == ROW_OUT_STRIP) {
         const int s = e / (B * W), w = e - s * (B * W);
-        a.dst[((z * (a.nx / W) + s) * a.ny + r0) * W + w] =
-            cscale(res[tix(s * W + (w & 3), w >> 2)], a.scale);
+        const int rl = w / W;
+        const int col = s * W + (w - rl * W);
+        a.dst[((z * nstrip + s) * a.ny + r0) * W + w] = cscale(res[col * LD + rl], a.scale);
       } else {
         const int rl = e / n, col = e - rl * n;
         const size_t gi = (z * a.ny + r0 + rl) * a.nx + col;
-        const float2 g = res[tix(col, rl)];
+        const float2 g = res[col * LD + rl];
         if (EPI == ROW_EPI_GRAD) {
           const float2 y = a.y[gi];
           a.dst[gi] = make_float2(y.x - a.scale * g.x, y.y - a.scale * g.y);
@@ -286,8 +249,8 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
-// Column pass: one strip of four columns; transforms along y.
-// grid (nx / 4, groups); group g covers planes [g*zpg, min(nz, (g+1)*zpg))
+// Column pass: one strip of kStrip columns; transforms along y.
+// grid (nx / kStrip, groups); group g covers planes [g*zpg, min(nz, (g+1)*zpg))
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 transfer(uint2 ph, float amp, int j) {
   const unsigned phi = ph.x + static_cast<unsigned>(j) * ph.y;   // wraps modulo 1 cycle
@@ -297,19 +260,18 @@ __device__ __forceinline__ float2 transfer(uint2 ph, float amp, int j) {
   return make_float2(amp * c, amp * s);
 }
 
-constexpr int kColMaxE = kMaxN * kStrip / kFftThreads;   // elements per thread
-
 template <int MODE>
 __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__ ColArgs a) {
   constexpr int B = kStrip;
+  constexpr int LD = B + 1;
   constexpr int T = kFftThreads;
-  constexpr int MAXE = kColMaxE;
+  constexpr int MAXE = kMaxN * B / T;
   extern __shared__ float2 smem[];
   const int n = a.ny;
   const int elems = n * B;
   float2* tile = smem;
-  float2* tile2 = smem + n * B;
-  float2* tw = smem + 2 * n * B;
+  float2* tile2 = smem + n * LD;
+  float2* tw = smem + 2 * n * LD;
   stage_twiddles(tw, a.tw, n);
 
   const int s = blockIdx.x;
@@ -322,35 +284,24 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
   if (MODE == COL_FWD_ZSUM) {
     const int z0 = blockIdx.y * a.z_per_group;
     const int z1 = min(a.nz, z0 + a.z_per_group);
-    float2 acc[MAXE], pre[MAXE];
+    float2 acc[MAXE];
 #pragma unroll
-    for (int q = 0; q < MAXE; ++q) {
-      acc[q] = make_float2(0.f, 0.f);
-      const int e = threadIdx.x + q * T;
-      if (e < elems && z0 < z1) pre[q] = a.src[(static_cast<size_t>(z0) * nstrip + s) * strip_elems + e];
-    }
+    for (int q = 0; q < MAXE; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int z = z0; z < z1; ++z) {
-#pragma unroll
-      for (int q = 0; q < MAXE; ++q) {
-        const int e = threadIdx.x + q * T;
-        if (e < elems) tile[tix(e >> 2, e & 3)] = pre[q];
+      const float2* src = a.src + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
+      for (int e = threadIdx.x; e < elems; e += T) {
+        const int r = e / B;
+        tile[r * LD + (e - r * B)] = src[e];
       }
       __syncthreads();
-      if (z + 1 < z1) {
-        const float2* src = a.src + (static_cast<size_t>(z + 1) * nstrip + s) * strip_elems;
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q) {
-          const int e = threadIdx.x + q * T;
-          if (e < elems) pre[q] = src[e];
-        }
-      }
-      const float2* res = fft_run<false>(tile, tile2, a.plan, tw);
+      const float2* res = fft_run<B, false>(tile, tile2, a.plan, tw);
 #pragma unroll
       for (int q = 0; q < MAXE; ++q) {
         const int e = threadIdx.x + q * T;
         if (e < elems) {
+          const int r = e / B;
           const float2 h = transfer(__ldg(ph_g + e), __ldg(amp_g + e), z);
-          acc[q] = cadd(acc[q], cmul(h, res[tix(e >> 2, e & 3)]));
+          acc[q] = cadd(acc[q], cmul(h, res[r * LD + (e - r * B)]));
         }
       }
       __syncthreads();
@@ -359,7 +310,10 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) {
       const int e = threadIdx.x + q * T;
-      if (e < elems) dst[static_cast<size_t>(e >> 2) * a.nx + s * B + (e & 3)] = acc[q];
+      if (e < elems) {
+        const int r = e / B;
+        dst[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)] = acc[q];
+      }
     }
   } else if (MODE == COL_ADJ_GEN) {
     const int z0 = blockIdx.y * a.z_per_group;
@@ -369,40 +323,56 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
     for (int q = 0; q < MAXE; ++q) {
       const int e = threadIdx.x + q * T;
       rr[q] = make_float2(0.f, 0.f);
-      if (e < elems)
-        rr[q] = cscale(a.src[static_cast<size_t>(e >> 2) * a.nx + s * B + (e & 3)], a.scale);
+      if (e < elems) {
+        const int r = e / B;
+        rr[q] = cscale(a.src[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)], a.scale);
+      }
     }
     for (int z = z0; z < z1; ++z) {
 #pragma unroll
       for (int q = 0; q < MAXE; ++q) {
         const int e = threadIdx.x + q * T;
         if (e < elems) {
+          const int r = e / B;
           const float2 h = transfer(__ldg(ph_g + e), __ldg(amp_g + e), z);
-          tile[tix(e >> 2, e & 3)] = cmulc(rr[q], h);
+          tile[r * LD + (e - r * B)] = cmulc(rr[q], h);
         }
       }
       __syncthreads();
-      const float2* res = fft_run<true>(tile, tile2, a.plan, tw);
+      const float2* res = fft_run<B, true>(tile, tile2, a.plan, tw);
       float2* dst = a.dst + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
-      for (int e = threadIdx.x; e < elems; e += T) dst[e] = res[tix(e >> 2, e & 3)];
+      for (int e = threadIdx.x; e < elems; e += T) {
+        const int r = e / B;
+        dst[e] = res[r * LD + (e - r * B)];
+      }
       __syncthreads();
     }
   } else if (MODE == COL_PLAIN_FWD) {
     // strip-major plane 0 -> row-major spectrum
     const float2* src = a.src + static_cast<size_t>(s) * strip_elems;
-    for (int e = threadIdx.x; e < elems; e += T) tile[tix(e >> 2, e & 3)] = src[e];
+    for (int e = threadIdx.x; e < elems; e += T) {
+      const int r = e / B;
+      tile[r * LD + (e - r * B)] = src[e];
+    }
     __syncthreads();
-    const float2* res = fft_run<false>(tile, tile2, a.plan, tw);
-    for (int e = threadIdx.x; e < elems; e += T)
-      a.dst[static_cast<size_t>(e >> 2) * a.nx + s * B + (e & 3)] =
-          cscale(res[tix(e >> 2, e & 3)], a.scale);
+    const float2* res = fft_run<B, false>(tile, tile2, a.plan, tw);
+    for (int e = threadIdx.x; e < elems; e += T) {
+      const int r = e / B;
+      a.dst[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)] =
+          cscale(res[r * LD + (e - r * B)], a.scale);
+    }
   } else {  // COL_PLAIN_INV: row-major spectrum -> strip-major plane 0
-    for (int e = threadIdx.x; e < elems; e += T)
-      tile[tix(e >> 2, e & 3)] = a.src[static_cast<size_t>(e >> 2) * a.nx + s * B + (e & 3)];
+    for (int e = threadIdx.x; e < elems; e += T) {
+      const int r = e / B;
+      tile[r * LD + (e - r * B)] = a.src[static_cast<size_t>(r) * a.nx + s * B + (e - r * B)];
+    }
     __syncthreads();
-    const float2* res = fft_run<true>(tile, tile2, a.plan, tw);
+    const float2* res = fft_run<B, true>(tile, tile2, a.plan, tw);
     float2* dst = a.dst + static_cast<size_t>(s) * strip_elems;
-    for (int e = threadIdx.x; e < elems; e += T) dst[e] = cscale(res[tix(e >> 2, e & 3)], a.scale);
+    for (int e = threadIdx.x; e < elems; e += T) {
+      const int r = e / B;
+      dst[e] = cscale(res[r * LD + (e - r * B)], a.scale);
+    }
   }
 }
 
@@ -471,7 +441,7 @@ cudaError_t launch_rows_t(const RowArgs& a, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int items = (a.ny / kRowsPerCta) * a.nz;
-  const int grid = items < 4 * sms ? items : 4 * sms;
+  const int grid = items < 2 * sms ? items : 2 * sms;
   kern<<<grid, kFftThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -491,12 +461,12 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 }  // namespace
 
 size_t rows_smem_bytes(int nx) {
-  return sizeof(float2) * (2 * static_cast<size_t>(nx) * kRowsPerCta + nx);
+  return sizeof(float2) * (2 * static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
 }
 
 size_t cols_smem_bytes(int mode, int ny) {
   (void)mode;
-  return sizeof(float2) * (2 * static_cast<size_t>(ny) * kStrip + ny);
+  return sizeof(float2) * (2 * static_cast<size_t>(ny) * (kStrip + 1) + ny);
 }
 
 cudaError_t launch_rows(int inv, int in, int out, int epi, const RowArgs& a, cudaStream_t s) {
