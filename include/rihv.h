@@ -148,6 +148,38 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
                         rihv_particle* out, int max_out, int* n_out);
 
+/* Batched solves. A batch groups handles (each with its own grid, optics,
+ * options and scratch; a handle may appear once) whose holograms are solved
+ * together: rihv_batch_solve runs every handle's complete FISTA solve (the
+ * same iteration count and lambdas for all) as one CUDA graph, one branch per
+ * handle, so the kernels of different holograms run concurrently and no
+ * launch returns to the host between iterations. The graph is captured on the
+ * first call and reused while iters, the lambdas, the presence of x0s and the
+ * handles' options and tuning stay the same. Not in the paper; it serves
+ * time-resolved sequences (many holograms per measurement).
+ * holograms[i]: host or device float32 hologram of handle i; x0s: NULL or an
+ * array of host or device warm-start volumes; x_outs[i]: host or device
+ * complex64 output volume; traces: NULL or per-handle host or device arrays
+ * of iters / check_every doubles (NULL entries allowed). Fixed iteration
+ * count: handles with f_star > 0 are rejected (RIHV_ERR_INVALID_ARG). The call
+ * returns after the batch has finished. */
+typedef struct rihv_batch_st* rihv_batch;
+rihv_status rihv_batch_create(const rihv_handle* handles, int n, rihv_batch* out);
+rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float lambda_l1,
+                             float lambda_tv, int iters, const void* const* x0s_or_null,
+                             void* const* x_outs, double* const* traces_or_null);
+rihv_status rihv_batch_destroy(rihv_batch b);
+
+/* Autotuner (not in the paper). Times, on the handle's own scratch, the TV
+ * kernel's z-chunk length (8..128 planes per CTA) and steps per launch (1 or
+ * 2, i.e. halo depth), and the number of planes each column-pass CTA sums
+ * (z-group size), then applies the fastest to the handle. With a non-NULL
+ * cache_path the result is looked up first (key: nx ny nz tv_dims) and
+ * appended after a search, one line per shape. chosen_or_null receives
+ * {z-chunk, steps per launch, planes per column group}. Synchronises; the
+ * scratch contents (x, y, v) are overwritten. */
+rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_null);
+
 /* Fused-lasso prox without any allocation. The paper has no counterpart to
  * this entry point; it exists for callers that cannot call cudaMalloc, such
  * as code running while a CUDA graph is captured, hosts that hand out device

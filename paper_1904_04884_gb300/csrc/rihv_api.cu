@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -108,6 +109,25 @@ struct rihv_ctx {
   std::vector<Rec> recs;
   double stage_ms[kNumStages] = {0};
   long long stage_launches[kNumStages] = {0};
+};
+
+// A batch of handles solved together: one CUDA graph runs every handle's
+// whole solve on its own branch (fork from a master stream, join back).
+struct rihv_batch_st {
+  std::vector<rihv_ctx*> hs;
+  cudaStream_t master = nullptr;
+  std::vector<cudaStream_t> branch;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+  // what the captured graph was built for
+  int iters = -1;
+  float l1 = -1.f, ltv = -1.f;
+  bool warm = false;
+  std::vector<rihv_options> opts;
+  std::vector<int> tunes;            // zchunk, zpg per handle
+  std::vector<std::vector<long long>> launches;   // per handle, per stage, per graph launch
+  std::vector<int> checks;           // objective checks per handle per launch
 };
 
 namespace {
@@ -354,6 +374,72 @@ rihv_status copy_in(rihv_ctx* h, void* dst, const void* src, size_t bytes) {
   return RIHV_OK;
 }
 
+rihv_status check_solve_args(rihv_ctx* h, float l1, float ltv, int iters) {
+  if (iters < 0 || !(l1 >= 0.f) || !(ltv >= 0.f) || !std::isfinite(l1) || !std::isfinite(ltv))
+    return fail(h, RIHV_ERR_INVALID_ARG, "iters >= 0 and finite lambdas >= 0 required");
+  return RIHV_OK;
+}
+
+rihv_status ensure_trace(rihv_ctx* h, int nchecks) {
+  if (nchecks <= h->trace_cap) return RIHV_OK;
+  if (h->trace) cudaFree(h->trace);
+  h->trace = nullptr;
+  h->trace_cap = 0;
+  if (cudaMalloc(&h->trace, sizeof(double) * nchecks) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RIHV_ERR_OOM, "trace allocation failed");
+  }
+  h->trace_cap = nchecks;
+  return RIHV_OK;
+}
+
+// Solve set-up from the hologram already in h->holo: F b, x_0 (zero unless
+// warm, in which case h->x already holds it), y_1 = x_0, scalars, flags.
+rihv_status enqueue_setup(rihv_ctx* h, bool warm) {
+  StageScope sc(h, ST_SETUP, 3);
+  CKS(fft2_plane(h, h->holo, true, h->bhat));
+  const size_t vb = h->nvox * sizeof(float2);
+  if (!warm) CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
+  CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
+  CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
+  return RIHV_OK;
+}
+
+// FISTA iteration k (1-based): forward and residual spectrum, gradient step,
+// fused-lasso prox with momentum and restart; every check_every iterations the
+// objective F(x_k) goes to trace slot *check, which is then incremented.
+rihv_status enqueue_iteration(rihv_ctx* h, int k, float lambda_l1, float lambda_tv, int* check) {
+  const float tau = static_cast<float>(h->tau);
+  const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
+  // (a) forward and residual spectrum R = F(H y - b)
+  CKS(forward_spectrum(h, h->y, h->bhat, h->spec));
+  // (c) v = y - tau * 2 H^H r
+  CKS(adjoint_planes(h, h->spec, h->y, h->v, grad_scale, true));
+  // (d) x_k = prox(v), momentum, restart
+  CKS(prox_into(h, h->v, tau * lambda_l1, tau * lambda_tv, h->opt.n_inner, FIN_FISTA, h->x));
+  const int M = h->opt.check_every;
+  if (M > 0 && k % M == 0) {
+    CKS(forward_spectrum(h, h->x, h->bhat, h->spec));
+    StageScope sc(h, ST_OBJECTIVE, 1);
+    CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, lambda_l1, lambda_tv, h->sc,
+                        h->red, h->trace + *check, h->stream));
+    ++*check;
+  }
+  return RIHV_OK;
+}
+
+// After the stream has finished: TV wait failures and non-finite reductions.
+rihv_status read_solve_errors(rihv_ctx* h) {
+  DevScalars hs{};
+  int tv_err = 0;
+  CK(cudaMemcpy(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&tv_err, h->tv_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tv_err) return fail(h, RIHV_ERR_TIMEOUT, "a TV kernel's bounded wait gave up");
+  if (hs.nonfinite) return fail(h, RIHV_ERR_NONFINITE, "a reduction produced NaN or Inf");
+  return RIHV_OK;
+}
+
 }  // namespace
 
 // =============================================================================
@@ -577,82 +663,36 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
                        int iters, const void* x0, void* x_out, double* trace, int* iters_done) {
   if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
   if (!hologram || !x_out) return fail(h, RIHV_ERR_INVALID_ARG, "hologram and x_out are required");
-  if (iters < 0 || !(lambda_l1 >= 0.f) || !(lambda_tv >= 0.f) || !std::isfinite(lambda_l1) ||
-      !std::isfinite(lambda_tv))
-    return fail(h, RIHV_ERR_INVALID_ARG, "iters >= 0 and finite lambdas >= 0 required");
+  CKS(check_solve_args(h, lambda_l1, lambda_tv, iters));
   if (is_device_ptr(x_out) && !aligned16(x_out))
     return fail(h, RIHV_ERR_INVALID_ARG, "x_out is not 16-byte aligned");
   const size_t vb = h->nvox * sizeof(float2);
   const int M = h->opt.check_every;
-  const int nchecks = (M > 0) ? iters / M : 0;
-  if (nchecks > h->trace_cap) {
-    if (h->trace) cudaFree(h->trace);
-    h->trace = nullptr;
-    h->trace_cap = 0;
-    if (cudaMalloc(&h->trace, sizeof(double) * nchecks) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(h, RIHV_ERR_OOM, "trace allocation failed");
-    }
-    h->trace_cap = nchecks;
-  }
+  CKS(ensure_trace(h, (M > 0) ? iters / M : 0));
   const bool stop_test = h->opt.f_star > 0.0 && M > 0;
 
-  {
-    // Hologram and its spectrum F b; x_0 and y_1 = x_0; scalars.
-    StageScope sc(h, ST_SETUP, 3);
-    CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
-    CKS(fft2_plane(h, h->holo, true, h->bhat));
-    if (x0)
-      CKS(copy_in(h, h->x, x0, vb));
-    else
-      CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
-    CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
-    CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
-    CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
-  }
-
-  const float tau = static_cast<float>(h->tau);
-  const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
+  CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
+  if (x0) CKS(copy_in(h, h->x, x0, vb));
+  CKS(enqueue_setup(h, x0 != nullptr));
   int done = 0;
   int check = 0;
   for (int k = 1; k <= iters; ++k) {
-    // (a) forward and residual spectrum R = F(H y - b)
-    CKS(forward_spectrum(h, h->y, h->bhat, h->spec));
-    // (c) v = y - tau * 2 H^H r
-    CKS(adjoint_planes(h, h->spec, h->y, h->v, grad_scale, true));
-    // (d) x_k = prox(v), momentum, restart
-    CKS(prox_into(h, h->v, tau * lambda_l1, tau * lambda_tv, h->opt.n_inner, FIN_FISTA, h->x));
+    const int before = check;
+    CKS(enqueue_iteration(h, k, lambda_l1, lambda_tv, &check));
     done = k;
-    if (M > 0 && k % M == 0) {
-      CKS(forward_spectrum(h, h->x, h->bhat, h->spec));
-      {
-        StageScope sc(h, ST_OBJECTIVE, 1);
-        CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, lambda_l1, lambda_tv, h->sc,
-                            h->red, h->trace + check, h->stream));
-      }
-      if (stop_test) {
-        double f = 0;
-        CK(cudaMemcpyAsync(&f, h->trace + check, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        ++check;
-        if (f <= h->opt.f_star * (1.0 + h->opt.tol)) break;
-      } else {
-        ++check;
-      }
+    if (stop_test && check > before) {
+      double f = 0;
+      CK(cudaMemcpyAsync(&f, h->trace + before, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (f <= h->opt.f_star * (1.0 + h->opt.tol)) break;
     }
   }
   CK(cudaMemcpyAsync(x_out, h->x, vb, cudaMemcpyDefault, h->stream));
   if (trace && check > 0)
     CK(cudaMemcpyAsync(trace, h->trace, sizeof(double) * check, cudaMemcpyDefault, h->stream));
-  DevScalars hs{};
-  int tv_err = 0;
-  CK(cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(&tv_err, h->tv_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (iters_done) *iters_done = done;
-  if (tv_err) return fail(h, RIHV_ERR_TIMEOUT, "a TV kernel's bounded wait gave up");
-  if (hs.nonfinite) return fail(h, RIHV_ERR_NONFINITE, "a reduction produced NaN or Inf");
-  return RIHV_OK;
+  return read_solve_errors(h);
 }
 
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
@@ -758,4 +798,296 @@ rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int
   return RIHV_OK;
 }
 
+// -----------------------------------------------------------------------------
+// Batched solves (one CUDA graph per batch)
+// -----------------------------------------------------------------------------
+rihv_status rihv_batch_create(const rihv_handle* hs, int n, rihv_batch* out) {
+  if (!hs || n <= 0 || !out) return fail(nullptr, RIHV_ERR_INVALID_ARG, "invalid batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle in batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(nullptr, RIHV_ERR_INVALID_ARG, "a handle appears twice");
+  }
+  rihv_batch b = new (std::nothrow) rihv_batch_st();
+  if (!b) return fail(nullptr, RIHV_ERR_OOM, "host allocation failed");
+  b->hs.assign(hs, hs + n);
+  bool ok = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  b->branch.resize(n, nullptr);
+  b->join.resize(n, nullptr);
+  for (int i = 0; ok && i < n; ++i)
+    ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    rihv_batch_destroy(b);
+    return fail(nullptr, RIHV_ERR_CUDA, "stream or event creation failed");
+  }
+  *out = b;
+  return RIHV_OK;
+}
+
+rihv_status rihv_batch_destroy(rihv_batch b) {
+  if (!b) return RIHV_OK;
+  if (b->master) cudaStreamSynchronize(b->master);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->master) cudaStreamDestroy(b->master);
+  delete b;
+  return RIHV_OK;
+}
+
+static bool same_options(const rihv_options& a, const rihv_options& o) {
+  return a.tv_dims == o.tv_dims && a.restart == o.restart && a.accelerate == o.accelerate &&
+         a.n_inner == o.n_inner && a.check_every == o.check_every &&
+         a.tv_steps_per_launch == o.tv_steps_per_launch;
+}
+
+static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, bool warm) {
+  const int n = static_cast<int>(b->hs.size());
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  std::vector<cudaStream_t> saved(n);
+  std::vector<bool> saved_prof(n);
+  b->launches.assign(n, std::vector<long long>(kNumStages, 0));
+  b->checks.assign(n, 0);
+  rihv_ctx* h0 = b->hs[0];
+  cudaError_t e = cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(h0, RIHV_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  cudaEventRecord(b->fork, b->master);
+  rihv_status st = RIHV_OK;
+  for (int i = 0; i < n && st == RIHV_OK; ++i) {
+    rihv_ctx* h = b->hs[i];
+    saved[i] = h->stream;
+    saved_prof[i] = h->prof;
+    h->stream = b->branch[i];
+    h->prof = false;
+    long long before[kNumStages];
+    for (int s = 0; s < kNumStages; ++s) before[s] = h->stage_launches[s];
+    cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    st = enqueue_setup(h, warm);
+    int check = 0;
+    for (int k = 1; k <= iters && st == RIHV_OK; ++k) st = enqueue_iteration(h, k, l1, ltv, &check);
+    b->checks[i] = check;
+    for (int s = 0; s < kNumStages; ++s) {
+      b->launches[i][s] = h->stage_launches[s] - before[s];
+      h->stage_launches[s] = before[s];   // counted per graph launch instead
+    }
+    cudaEventRecord(b->join[i], b->branch[i]);
+    cudaStreamWaitEvent(b->master, b->join[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(b->master, &graph);
+  for (int i = 0; i < n; ++i) {
+    if (!saved.empty() && i < static_cast<int>(saved.size()) && b->hs[i]->stream == b->branch[i]) {
+      b->hs[i]->stream = saved[i];
+      b->hs[i]->prof = saved_prof[i];
+    }
+  }
+  if (st != RIHV_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(h0, RIHV_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return fail(h0, RIHV_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  b->iters = iters;
+  b->l1 = l1;
+  b->ltv = ltv;
+  b->warm = warm;
+  b->opts.clear();
+  b->tunes.clear();
+  for (auto* h : b->hs) {
+    b->opts.push_back(h->opt);
+    b->tunes.push_back(h->tv_zchunk);
+    b->tunes.push_back(h->zpg);
+  }
+  return RIHV_OK;
+}
+
+rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float lambda_l1,
+                             float lambda_tv, int iters, const void* const* x0s, void* const* x_outs,
+                             double* const* traces) {
+  if (!b) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null batch");
+  const int n = static_cast<int>(b->hs.size());
+  rihv_ctx* h0 = b->hs[0];
+  if (!holograms || !x_outs) return fail(h0, RIHV_ERR_INVALID_ARG, "holograms and x_outs required");
+  for (int i = 0; i < n; ++i) {
+    rihv_ctx* h = b->hs[i];
+    if (!holograms[i] || !x_outs[i]) return fail(h, RIHV_ERR_INVALID_ARG, "null hologram or x_out");
+    CKS(check_solve_args(h, lambda_l1, lambda_tv, iters));
+    if (h->opt.f_star > 0.0)
+      return fail(h, RIHV_ERR_INVALID_ARG, "batched solves run a fixed iteration count (f_star must be 0)");
+    const int M = h->opt.check_every;
+    CKS(ensure_trace(h, (M > 0) ? iters / M : 0));
+  }
+  const bool warm = x0s != nullptr;
+  bool recapture = !b->exec || b->iters != iters || b->l1 != lambda_l1 || b->ltv != lambda_tv ||
+                   b->warm != warm;
+  for (int i = 0; i < n && !recapture; ++i) {
+    rihv_ctx* h = b->hs[i];
+    recapture = !same_options(b->opts[i], h->opt) || b->tunes[2 * i] != h->tv_zchunk ||
+                b->tunes[2 * i + 1] != h->zpg;
+  }
+  // inputs into each handle's own buffers (outside the graph)
+  for (int i = 0; i < n; ++i) {
+    rihv_ctx* h = b->hs[i];
+    CK(cudaMemcpyAsync(h->holo, holograms[i], h->nxy * sizeof(float), cudaMemcpyDefault, b->master));
+    if (warm) {
+      if (!x0s[i]) return fail(h, RIHV_ERR_INVALID_ARG, "x0s given but x0s[i] is NULL");
+      CK(cudaMemcpyAsync(h->x, x0s[i], h->nvox * sizeof(float2), cudaMemcpyDefault, b->master));
+    }
+  }
+  if (recapture) CKS(batch_capture(b, lambda_l1, lambda_tv, iters, warm));
+  rihv_ctx* h = h0;
+  CK(cudaGraphLaunch(b->exec, b->master));
+  for (int i = 0; i < n; ++i) {
+    rihv_ctx* hi = b->hs[i];
+    for (int s = 0; s < kNumStages; ++s) hi->stage_launches[s] += b->launches[i][s];
+    CK(cudaMemcpyAsync(x_outs[i], hi->x, hi->nvox * sizeof(float2), cudaMemcpyDefault, b->master));
+    if (traces && traces[i] && b->checks[i] > 0)
+      CK(cudaMemcpyAsync(traces[i], hi->trace, sizeof(double) * b->checks[i], cudaMemcpyDefault,
+                         b->master));
+  }
+  CK(cudaStreamSynchronize(b->master));
+  for (auto* hi : b->hs) CKS(read_solve_errors(hi));
+  return RIHV_OK;
+}
+
+// -----------------------------------------------------------------------------
+// Autotuner
+// -----------------------------------------------------------------------------
+static double time_ms(rihv_ctx* h, const std::function<rihv_status()>& fn, int reps,
+                      rihv_status* st) {
+  cudaEvent_t a, c;
+  cudaEventCreate(&a);
+  cudaEventCreate(&c);
+  *st = fn();   // warm-up
+  std::vector<float> t;
+  for (int r = 0; r < reps && *st == RIHV_OK; ++r) {
+    cudaEventRecord(a, h->stream);
+    *st = fn();
+    cudaEventRecord(c, h->stream);
+    cudaEventSynchronize(c);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, c);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(c);
+  if (t.empty()) return 1e30;
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  char key[96];
+  snprintf(key, sizeof(key), "rihv-tune-v1 %d %d %d %d", h->nx, h->ny, h->nz, h->opt.tv_dims);
+  int zchunk = -1, per = -1, zpg = -1;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[256];
+      while (fgets(line, sizeof(line), f)) {
+        int a = 0, b2 = 0, c = 0;
+        const size_t kl = strlen(key);
+        if (strncmp(line, key, kl) == 0 && line[kl] == ':' &&
+            sscanf(line + kl + 1, "%d %d %d", &a, &b2, &c) == 3 && a >= 1 && (b2 == 1 || b2 == 2) &&
+            c >= 1 && c <= h->nz && (h->nz + c - 1) / c <= kMaxGroups) {
+          zchunk = a;
+          per = b2;
+          zpg = c;
+        }
+      }
+      fclose(f);
+    }
+  }
+  if (zchunk < 0) {
+    // Search on the handle's own buffers (values do not change the timing).
+    CK(cudaMemsetAsync(h->v, 0, h->nvox * sizeof(float2), h->stream));
+    CK(cudaMemsetAsync(h->y, 0, h->nvox * sizeof(float2), h->stream));
+    CK(cudaMemsetAsync(h->spec, 0, h->nxy * sizeof(float2), h->stream));
+    const bool prof = h->prof;
+    h->prof = false;
+    const rihv_options saved = h->opt;
+    const int saved_zc = h->tv_zchunk, saved_zpg = h->zpg, saved_g = h->groups;
+    rihv_status st = RIHV_OK;
+    double best = 1e30;
+    const int kSteps = 4;
+    for (int p = 1; p <= 2; ++p) {
+      for (int zc : {8, 16, 32, 64, 128}) {
+        if (zc > h->nz && zc != 8) continue;
+        h->opt.tv_steps_per_launch = p;
+        h->tv_zchunk = zc;
+        float2* const* pf = nullptr;
+        const double t = time_ms(h, [&] { return tv_steps(h, h->v, 1e-3f, kSteps, &pf); }, 3, &st);
+        if (st != RIHV_OK) break;
+        if (t < best * 0.99) {
+          best = t;
+          zchunk = zc;
+          per = p;
+        }
+      }
+    }
+    // column-pass z-groups: the wave-filling default and its neighbours
+    best = 1e30;
+    std::vector<int> cands;
+    for (int g : {saved_g - 2, saved_g - 1, saved_g, saved_g + 1, saved_g + 2, 2 * saved_g}) {
+      if (g < 1 || g > kMaxGroups || g > h->nz) continue;
+      const int c = (h->nz + g - 1) / g;
+      if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+    }
+    const float gs = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
+    for (int c : cands) {
+      if (st != RIHV_OK) break;
+      h->zpg = c;
+      h->groups = (h->nz + c - 1) / c;
+      const double t = time_ms(h, [&] {
+        rihv_status s2 = forward_spectrum(h, h->y, nullptr, h->spec);
+        if (s2 != RIHV_OK) return s2;
+        return adjoint_planes(h, h->spec, h->y, h->v, gs, true);
+      }, 3, &st);
+      if (t < best * 0.99) {
+        best = t;
+        zpg = c;
+      }
+    }
+    h->opt = saved;
+    h->tv_zchunk = saved_zc;
+    h->zpg = saved_zpg;
+    h->groups = saved_g;
+    h->prof = prof;
+    // reset the launch counters the search added
+    for (int s = 0; s < kNumStages; ++s) h->stage_launches[s] = 0;
+    if (st != RIHV_OK) return st;
+    if (cache_path) {
+      if (FILE* f = fopen(cache_path, "a")) {
+        fprintf(f, "%s: %d %d %d\n", key, zchunk, per, zpg);
+        fclose(f);
+      }
+    }
+  }
+  h->tv_zchunk = zchunk;
+  h->opt.tv_steps_per_launch = per;
+  h->zpg = zpg;
+  h->groups = (h->nz + zpg - 1) / zpg;
+  if (chosen) {
+    chosen[0] = zchunk;
+    chosen[1] = per;
+    chosen[2] = zpg;
+  }
+  return RIHV_OK;
+}
+
 }  // extern "C"
+

@@ -24,7 +24,8 @@ STATUS = {0: "RIHV_OK", 1: "RIHV_ERR_INVALID_ARG", 2: "RIHV_ERR_CUDA", 3: "RIHV_
 EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stream",
            "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
            "rihv_solve", "rihv_detect", "rihv_set_profiling", "rihv_stage_times",
-           "rihv_step_size", "rihv_last_error"]
+           "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
+           "rihv_batch_destroy", "rihv_autotune"]
 
 STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup"]
 
@@ -77,6 +78,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_stage_times": (i, [H, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "rihv_step_size": (i, [H, ctypes.POINTER(d)]),
         "rihv_last_error": (ctypes.c_char_p, [H]),
+        "rihv_batch_create": (i, [ctypes.POINTER(H), i, ctypes.POINTER(H)]),
+        "rihv_batch_solve": (i, [H, ctypes.POINTER(vp), f, f, i, ctypes.POINTER(vp),
+                                 ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "rihv_batch_destroy": (i, [H]),
+        "rihv_autotune": (i, [H, ctypes.c_char_p, ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -212,6 +218,17 @@ class Rihv:
                             first=p.first))
         return out
 
+    def rihv_autotune(self, cache_path=None):
+        """Times the TV z-chunk / steps per launch and the column-pass z-groups on
+        this handle and applies the fastest; returns (z_chunk, steps_per_launch,
+        planes_per_group). With cache_path the result is looked up / stored."""
+        out = (ctypes.c_int * 3)()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.L.rihv_autotune(self.h, path, out), self.h)
+        return tuple(out)
+
+    autotune = rihv_autotune
+
     # -- profiling ----------------------------------------------------------
     def set_profiling(self, on: bool):
         self._check(self.L.rihv_set_profiling(self.h, 1 if on else 0), self.h)
@@ -229,6 +246,49 @@ class Rihv:
     prox_fused_lasso = rihv_prox_fused_lasso
     solve = rihv_solve
     detect = rihv_detect
+
+
+class Batch:
+    """Handles solved together as one CUDA graph (rihv_batch_*)."""
+
+    def __init__(self, handles):
+        self.L = load_library()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        st = self.L.rihv_batch_create(arr, len(self.handles), ctypes.byref(b))
+        if st != 0:
+            raise RihvError(st, self.L.rihv_last_error(None).decode())
+        self.b = b
+
+    def solve(self, holograms, lambda_l1, lambda_tv, iters, x_outs, x0s=None, traces=None):
+        n = len(self.handles)
+        vp = ctypes.c_void_p
+        holo = (vp * n)(*[_ptr(g, dtype="float32", numel=h.nxy, name="hologram")
+                          for g, h in zip(holograms, self.handles)])
+        outs = (vp * n)(*[_ptr(x, dtype="complex64", numel=h.nvox, name="x_out")
+                          for x, h in zip(x_outs, self.handles)])
+        x0 = None if x0s is None else (vp * n)(*[_ptr(x, dtype="complex64", numel=h.nvox,
+                                                      name="x0")
+                                                 for x, h in zip(x0s, self.handles)])
+        tr = None if traces is None else (vp * n)(*[_ptr(t, dtype="float64", name="trace")
+                                                    for t in traces])
+        st = self.L.rihv_batch_solve(self.b, holo, float(lambda_l1), float(lambda_tv), int(iters),
+                                     x0, outs, tr)
+        if st != 0:
+            msgs = [self.L.rihv_last_error(h.h).decode() for h in self.handles]
+            raise RihvError(st, "; ".join(m for m in msgs if m))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.L.rihv_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rihv_prox_fused_lasso_noalloc(v, x_out, nz, ny, nx, tv_dims, t_l1, t_tv, inner_iters,
