@@ -1,0 +1,446 @@
+// 3x3x3 convolutions of the warm-start network on 5th-generation tensor cores
+// (tcgen05, BF16 operands, FP32 accumulators in tensor memory).
+//
+// Activations are channels-last, [voxel][channel] in BF16, voxel = (z*H + y)*W + x.
+// Weights are W[c_out][tap][c_in], tap = (dz+1)*9 + (dy+1)*3 + (dx+1).
+//
+// Forward and input gradient (implicit GEMM, one CTA per 128 output voxels):
+//   D[m][n] = sum_tap sum_k A_tap[m][k] B_tap[n][k]
+//   forward : A = X[v_m + off_tap][k],  B = W[n][tap][k]            (n = c_out)
+//   dgrad   : A = dY[v_m + off_tap][k], B = W[k][26 - tap][n]       (n = c_in)
+// Each tap is one K stage of C_k channels. The stage's A (gathered by the 128
+// threads, one output voxel each, zero outside the volume) and B tiles are
+// written to shared memory in the canonical K-major no-swizzle layout (8x16-byte
+// core matrices; LBO = 128 B along K, SBO = C_k*16 B along M/N), double
+// buffered; one thread issues C_k/16 tcgen05.mma (M = 128, N = C_out, K = 16)
+// into the TMEM accumulator and commits to the stage's mbarrier, which frees
+// the buffer two stages later. The epilogue reads TMEM with tcgen05.ld (warp w
+// owns lanes 32w..32w+31 = its 32 voxels), adds the bias, applies ReLU and
+// stores BF16 or FP32.
+//
+// Weight gradient (K = voxels, split over CTAs):
+//   D[m][n] = sum_v A[m][v] B[n][v],  m = tap*C_in + c,  n = c_out
+//   A[m][v] = X[v + off_tap][c],  B[n][v] = dY[v][n]
+// Both operands are MN-major here (for a fixed voxel the channels are
+// contiguous in memory), staged as 8 (voxel) x 16-byte (8 channel) core
+// matrices (SBO = 128 B along M/N, LBO along K). Each CTA accumulates 128 rows
+// over its voxel range and writes FP32 partials that a second kernel sums in a
+// fixed order.
+//
+// All waits are bounded: on timeout the CTA records an error, waits (bounded)
+// for its issued MMAs, releases its tensor memory and exits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rihv_internal.cuh"
+
+namespace rihv {
+namespace {
+
+constexpr int kM = 128;                // voxels per CTA tile (MMA M)
+constexpr int kThreads = 128;
+constexpr int kWaitLimit = 1 << 22;
+constexpr int kWgK = 64;               // voxels per weight-gradient K stage
+
+// ---- PTX helpers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_slot),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading byte
+// offset (along K), stride byte offset (along M/N), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// A/B major-ness (0 = K-major, 1 = MN-major), N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t mma_idesc(int m, int n, int a_mn_major, int b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn_major) << 15) |
+         (static_cast<uint32_t>(b_mn_major) << 16) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t tmem_cols(int n) {
+  uint32_t c = 32;
+  while (c < static_cast<uint32_t>(n)) c <<= 1;
+  return c;
+}
+
+__device__ __forceinline__ void tap_offset(int t, int& dz, int& dy, int& dx) {
+  dz = t / 9 - 1;
+  dy = (t / 3) % 3 - 1;
+  dx = t % 3 - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Forward / input-gradient kernel
+// ---------------------------------------------------------------------------
+template <bool DGRAD>
+__global__ void __launch_bounds__(kThreads) k_conv_igemm(const __grid_constant__ ConvArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int ck = a.ck;                  // channels of the gathered input (K per tap)
+  const int n = a.n;                    // output channels (MMA N)
+  const int ku = ck / 8;                // 16-byte K units per row
+  const uint32_t a_bytes = kM * ck * 2;
+  const uint32_t b_bytes = n * ck * 2;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  unsigned char* stage0 = smem + 128;
+  unsigned char* sa[2] = {stage0, stage0 + a_bytes + b_bytes};
+  unsigned char* sb[2] = {stage0 + a_bytes, stage0 + 2 * a_bytes + b_bytes};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tmem_cols(n);
+
+  if (tid == 0) {
+    mbar_init(saddr(&bars[0]), 1);
+    mbar_init(saddr(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(tmem_slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
+  const size_t v = static_cast<size_t>(blockIdx.x) * kM + tid;
+  const bool vvalid = v < nvox;
+  const int x = static_cast<int>(v % a.w);
+  const int y = static_cast<int>((v / a.w) % a.h);
+  const int z = static_cast<int>(v / (static_cast<size_t>(a.w) * a.h));
+  const int g = tid >> 3, r = tid & 7;
+  const uint32_t idesc = mma_idesc(kM, n, 0, 0);
+  const uint32_t sbo = ku * 128;
+  bool ok = true;
+  int issued = -1;
+
+  for (int t = 0; t < 27 && ok; ++t) {
+    const int buf = t & 1;
+    if (t >= 2) {
+      const bool w_ok = mbar_wait(saddr(&bars[buf]), ((t - 2) >> 1) & 1);
+      ok = __syncthreads_and(w_ok) != 0;
+      if (!ok) break;
+    }
+    int dz, dy, dx;
+    tap_offset(t, dz, dy, dx);
+    // A: this thread's voxel row
+    {
+      const int zz = z + dz, yy = y + dy, xx = x + dx;
+      const bool inb = vvalid && zz >= 0 && zz < a.d && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+      const uint4* src = reinterpret_cast<const uint4*>(
+          a.x + (inb ? ((static_cast<size_t>(zz) * a.h + yy) * a.w + xx) * ck : 0));
+      unsigned char* dst = sa[buf] + g * ku * 128 + r * 16;
+      for (int k = 0; k < ku; ++k) {
+        const uint4 val = inb ? __ldg(src + k) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(dst + k * 128) = val;
+      }
+    }
+    // B: weights of this tap
+    for (int u = tid; u < n * ku; u += kThreads) {
+      const int nn = u / ku, k = u - nn * ku;
+      uint4 val;
+      if (!DGRAD) {
+        val = __ldg(reinterpret_cast<const uint4*>(a.w_ + (static_cast<size_t>(nn) * 27 + t) * ck) + k);
+      } else {
+        // W is [ck = c_out][27][n = c_in]; B[nn][kk] = W[kk][26 - t][nn]
+        uint16_t e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int kk = k * 8 + j;
+          e[j] = reinterpret_cast<const uint16_t*>(a.w_)[(static_cast<size_t>(kk) * 27 + (26 - t)) * n + nn];
+        }
+        val = make_uint4(e[0] | (static_cast<uint32_t>(e[1]) << 16), e[2] | (static_cast<uint32_t>(e[3]) << 16),
+                         e[4] | (static_cast<uint32_t>(e[5]) << 16), e[6] | (static_cast<uint32_t>(e[7]) << 16));
+      }
+      *reinterpret_cast<uint4*>(sb[buf] + ((nn >> 3) * ku + k) * 128 + (nn & 7) * 16) = val;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = saddr(sa[buf]), b0 = saddr(sb[buf]);
+      for (int s = 0; s < ck / 16; ++s)
+        umma_bf16(tmem, smem_desc(a0 + s * 256, 128, sbo), smem_desc(b0 + s * 256, 128, sbo), idesc,
+                  (t > 0 || s > 0) ? 1u : 0u);
+      umma_commit(saddr(&bars[buf]));
+    }
+    issued = t;
+  }
+
+  // all MMAs done: the commit after the last issued stage
+  if (issued >= 0) {
+    const bool w_ok = mbar_wait(saddr(&bars[issued & 1]), (issued >> 1) & 1);
+    ok = (__syncthreads_and(w_ok) != 0) && ok;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+    return;
+  }
+  tc_fence_after();
+  // epilogue: warp w reads TMEM lanes 32w..32w+31 (its voxels)
+  const size_t vo = static_cast<size_t>(blockIdx.x) * kM + warp * 32 + lane;
+  for (int c0 = 0; c0 < n; c0 += 8) {
+    float acc[8];
+    tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, acc);
+    if (vo < nvox) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (a.bias) acc[j] += a.bias[c0 + j];
+        if (a.relu) acc[j] = fmaxf(acc[j], 0.f);
+      }
+      if (a.out_f32) {
+        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vo * n + c0);
+        dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      } else {
+        __nv_bfloat162 p[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
+        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vo * n + c0) =
+            *reinterpret_cast<uint4*>(p);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Weight-gradient kernel: grid (m tiles, voxel splits)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad(const __grid_constant__ WgradArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int cin = a.cin, n = a.cout;
+  const int ng = n / 8;
+  const uint32_t a_bytes = kM * kWgK * 2;   // 16 KB
+  const uint32_t b_bytes = n * kWgK * 2;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  unsigned char* stage0 = smem + 128;
+  unsigned char* sa[2] = {stage0, stage0 + a_bytes + b_bytes};
+  unsigned char* sb[2] = {stage0 + a_bytes, stage0 + 2 * a_bytes + b_bytes};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tmem_cols(n);
+
+  if (tid == 0) {
+    mbar_init(saddr(&bars[0]), 1);
+    mbar_init(saddr(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(tmem_slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
+  const int m0 = blockIdx.x * kM;
+  const int mtot = 27 * cin;
+  const size_t v0 = static_cast<size_t>(blockIdx.y) * a.vox_per_split;
+  const size_t v1 = v0 + a.vox_per_split < nvox ? v0 + a.vox_per_split : nvox;
+  const int nstages = static_cast<int>((v1 > v0 ? v1 - v0 : 0) + kWgK - 1) / kWgK;
+  const uint32_t idesc = mma_idesc(kM, n, 1, 1);
+  bool ok = true;
+  int issued = -1;
+
+  for (int st = 0; st < nstages && ok; ++st) {
+    const int buf = st & 1;
+    if (st >= 2) {
+      const bool w_ok = mbar_wait(saddr(&bars[buf]), ((st - 2) >> 1) & 1);
+      ok = __syncthreads_and(w_ok) != 0;
+      if (!ok) break;
+    }
+    const size_t vs = v0 + static_cast<size_t>(st) * kWgK;
+    // A: 8 voxel groups x 16 channel groups x 8 voxels, unit = 8 channels
+    for (int u = tid; u < (kWgK / 8) * 16 * 8; u += kThreads) {
+      const int r = u & 7, mg = (u >> 3) & 15, kg = u >> 7;
+      const size_t vv = vs + kg * 8 + r;
+      const int m = m0 + mg * 8;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (vv < v1 && m < mtot) {
+        const int t = m / cin, c = m - t * cin;
+        int dz, dy, dx;
+        tap_offset(t, dz, dy, dx);
+        const int x = static_cast<int>(vv % a.w) + dx;
+        const int y = static_cast<int>((vv / a.w) % a.h) + dy;
+        const int z = static_cast<int>(vv / (static_cast<size_t>(a.w) * a.h)) + dz;
+        if (z >= 0 && z < a.d && y >= 0 && y < a.h && x >= 0 && x < a.w)
+          val = __ldg(reinterpret_cast<const uint4*>(
+              a.x + ((static_cast<size_t>(z) * a.h + y) * a.w + x) * cin + c));
+      }
+      *reinterpret_cast<uint4*>(sa[buf] + (kg * 16 + mg) * 128 + r * 16) = val;
+    }
+    // B: dY rows of these voxels
+    for (int u = tid; u < (kWgK / 8) * ng * 8; u += kThreads) {
+      const int r = u & 7, gq = (u >> 3) % ng, kg = (u >> 3) / ng;
+      const size_t vv = vs + kg * 8 + r;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (vv < v1) val = __ldg(reinterpret_cast<const uint4*>(a.gy + vv * n + gq * 8));
+      *reinterpret_cast<uint4*>(sb[buf] + (kg * ng + gq) * 128 + r * 16) = val;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = saddr(sa[buf]), b0 = saddr(sb[buf]);
+      for (int s = 0; s < kWgK / 16; ++s)
+        umma_bf16(tmem, smem_desc(a0 + s * 2 * 2048, 2048, 128),
+                  smem_desc(b0 + s * 2 * ng * 128, ng * 128, 128), idesc, (st > 0 || s > 0) ? 1u : 0u);
+      umma_commit(saddr(&bars[buf]));
+    }
+    issued = st;
+  }
+  if (issued >= 0) {
+    const bool w_ok = mbar_wait(saddr(&bars[issued & 1]), (issued >> 1) & 1);
+    ok = (__syncthreads_and(w_ok) != 0) && ok;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+    return;
+  }
+  tc_fence_after();
+  const int row = warp * 32 + lane;
+  float* dst = a.partial + (static_cast<size_t>(blockIdx.y) * gridDim.x * kM + m0 + row) * n;
+  for (int c0 = 0; c0 < n; c0 += 8) {
+    float acc[8];
+    if (issued >= 0) {
+      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    }
+    float4* d4 = reinterpret_cast<float4*>(dst + c0);
+    d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// gW[o][t][c] = sum over splits of partial[split][t*cin + c][o] (fixed order)
+__global__ void k_wgrad_reduce(const float* partial, int nsplit, int mpad, int cin, int cout,
+                               float* gw) {
+  const int total = cout * 27 * cin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int o = i / (27 * cin);
+    const int m = i - o * 27 * cin;   // t*cin + c
+    float s = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) s += partial[(static_cast<size_t>(sp) * mpad + m) * cout + o];
+    gw[i] = s;
+  }
+}
+
+}  // namespace
+
+size_t conv_smem_bytes(int ck, int n) { return 128 + 2 * (static_cast<size_t>(kM) * ck * 2 + n * ck * 2); }
+size_t wgrad_smem_bytes(int cout) { return 128 + 2 * (static_cast<size_t>(kM) * kWgK * 2 + cout * kWgK * 2); }
+
+cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s) {
+  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
+  const unsigned grid = static_cast<unsigned>((nvox + kM - 1) / kM);
+  const size_t smem = conv_smem_bytes(a.ck, a.n);
+  auto kern = dgrad ? k_conv_igemm<true> : k_conv_igemm<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t* vps) {
+  *mtiles = (27 * cin + kM - 1) / kM;
+  int ns = (4 * sms + *mtiles - 1) / *mtiles;
+  const size_t per = (nvox + ns - 1) / ns;
+  *vps = ((per + kWgK - 1) / kWgK) * kWgK;
+  if (*vps == 0) *vps = kWgK;
+  *nsplit = static_cast<int>((nvox + *vps - 1) / *vps);
+  if (*nsplit < 1) *nsplit = 1;
+}
+
+cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s) {
+  dim3 grid(a.mtiles, a.nsplit);
+  const size_t smem = wgrad_smem_bytes(a.cout);
+  cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_conv_wgrad<<<grid, kThreads, smem, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_wgrad_reduce<<<128, 256, 0, s>>>(a.partial, a.nsplit, a.mtiles * kM, a.cin, a.cout, gw);
+  return cudaGetLastError();
+}
+
+}  // namespace rihv

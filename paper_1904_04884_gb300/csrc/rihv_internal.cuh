@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -162,5 +163,32 @@ cudaError_t detect_label(const float2* x, int nx, int ny, int nz, float rel, Det
 // Component ids, first indices and FP64 sums for ncomp <= w.capacity components.
 cudaError_t detect_stats(const float2* x, int nx, int ny, int nz, DetectWork& w, int ncomp,
                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Warm-start network convolutions (conv_kernels.cu)
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+  const __nv_bfloat16* x;   // [voxels][ck] (forward: input; dgrad: output gradient)
+  const __nv_bfloat16* w_;  // W[c_out][27][c_in]
+  const float* bias;        // [n] or null
+  void* y;                  // [voxels][n], BF16 or FP32
+  int d, h, w;              // volume (z, y, x) sizes
+  int ck, n;                // gathered channels (K per tap), output channels (N)
+  int relu, out_f32;
+  int* err;
+};
+struct WgradArgs {
+  const __nv_bfloat16* x;   // [voxels][cin]
+  const __nv_bfloat16* gy;  // [voxels][cout]
+  float* partial;           // [nsplit][mtiles*128][cout]
+  int d, h, w, cin, cout;
+  int mtiles, nsplit;
+  size_t vox_per_split;
+  int* err;
+};
+cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s);
+void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t* vps);
+cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s);
+size_t conv_smem_bytes(int ck, int n);
 
 }  // namespace rihv

@@ -8,12 +8,15 @@ import pytest
 from paper_1904_04884_gb300 import build as B
 from paper_1904_04884_gb300 import rihv
 
-HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rihv.h")
+INC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
 
 
 def declared():
-    txt = open(HDR).read()
-    return sorted(set(re.findall(r"\b(rihv_[a-z_]+)\s*\(", txt)))
+    names = set()
+    for f in os.listdir(INC):
+        if f.endswith(".h"):
+            names |= set(re.findall(r"\b(rihv_[a-z0-9_]+)\s*\(", open(os.path.join(INC, f)).read()))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
