@@ -78,6 +78,10 @@ rihv_status rihv_nn_upsample2(const uint16_t* x, uint16_t* y, int d, int h, int 
 rihv_status rihv_nn_upsample2_grad(const uint16_t* gy, uint16_t* gx, int d, int h, int wd, int c,
                                    void* stream);
 
+/* out = a + b over n BF16 values (gradient accumulation at skip connections). */
+rihv_status rihv_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n,
+                        void* stream);
+
 /* Channel concatenation out[v] = (a[v], b[v]) and its adjoint (split). */
 rihv_status rihv_nn_concat(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t voxels,
                            int ca, int cb, void* stream);

@@ -95,6 +95,12 @@ __global__ void k_upsample2_grad(const uint16_t* gy, uint16_t* gx, int d, int h,
   }
 }
 
+__global__ void k_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    out[i] = to_bf(bf(a[i]) + bf(b[i]));
+}
+
 __global__ void k_concat(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t voxels, int ca,
                          int cb) {
   const int c = ca + cb;
@@ -354,6 +360,13 @@ rihv_status rihv_nn_upsample2_grad(const uint16_t* gy, uint16_t* gx, int d, int 
   if (!gy || !gx || d < 1 || h < 1 || wd < 1 || c < 1) return RIHV_ERR_INVALID_ARG;
   const size_t n = static_cast<size_t>(d) * h * wd * c;
   k_upsample2_grad<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(gy, gx, d, h, wd, c);
+  return launched();
+}
+
+rihv_status rihv_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n,
+                        void* stream) {
+  if (!a || !b || !out) return RIHV_ERR_INVALID_ARG;
+  k_add<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, out, n);
   return launched();
 }
 

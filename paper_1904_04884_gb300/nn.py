@@ -28,6 +28,7 @@ def _lib():
             "rihv_nn_avgpool2_grad": (i, [vp, vp, i, i, i, i, vp]),
             "rihv_nn_upsample2": (i, [vp, vp, i, i, i, i, vp]),
             "rihv_nn_upsample2_grad": (i, [vp, vp, i, i, i, i, vp]),
+            "rihv_nn_add": (i, [vp, vp, vp, sz, vp]),
             "rihv_nn_concat": (i, [vp, vp, vp, sz, i, i, vp]),
             "rihv_nn_split": (i, [vp, vp, vp, sz, i, i, vp]),
             "rihv_nn_pack_input": (i, [vp, vp, sz, i, f, vp]),
@@ -105,6 +106,10 @@ def upsample2(x, y, dims, c):
 
 def upsample2_grad(gy, gx, dims, c):
     _ok(_lib().rihv_nn_upsample2_grad(_p(gy), _p(gx), *dims, c, _stream()), "rihv_nn_upsample2_grad")
+
+
+def add(a, b, out):
+    _ok(_lib().rihv_nn_add(_p(a), _p(b), _p(out), a.numel(), _stream()), "rihv_nn_add")
 
 
 def concat(a, b, out, voxels, ca, cb):
