@@ -93,10 +93,11 @@ rihv_status rihv_nn_split(const uint16_t* g, uint16_t* ga, uint16_t* gb, size_t 
 rihv_status rihv_nn_pack_input(const void* vol_c64, uint16_t* out, size_t voxels, int c,
                                float scale, void* stream);
 
-/* Complex64 volume from the network output: vol = scale * (y0 + i y1) where
- * y is FP32 [v][c]. */
-rihv_status rihv_nn_unpack_output(const float* y, void* vol_c64, size_t voxels, int c,
-                                  float scale, void* stream);
+/* Complex64 volume from the network output: vol = scale * (y0 + i y1)
+ * + base_scale * base, where y is FP32 [v][c] and base an optional complex64
+ * volume (NULL: no base term). vol may alias base. */
+rihv_status rihv_nn_unpack_output(const float* y, const void* base_c64, float base_scale,
+                                  void* vol_c64, size_t voxels, int c, float scale, void* stream);
 
 /* Mean squared error between the output (channels 0 and 1 of FP32 y [v][c])
  * and target/scale (complex64 volume): loss = mean over voxels of

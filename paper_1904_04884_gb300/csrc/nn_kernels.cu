@@ -140,10 +140,18 @@ __global__ void k_pack_input(const float2* vol, uint16_t* out, size_t voxels, in
   }
 }
 
-__global__ void k_unpack_output(const float* y, float2* vol, size_t voxels, int c, float scale) {
+__global__ void k_unpack_output(const float* y, const float2* base, float base_scale, float2* vol,
+                                size_t voxels, int c, float scale) {
   for (size_t v = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; v < voxels;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x)
-    vol[v] = make_float2(scale * y[v * c], scale * y[v * c + 1]);
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    float2 o = make_float2(scale * y[v * c], scale * y[v * c + 1]);
+    if (base) {
+      const float2 b = base[v];
+      o.x += base_scale * b.x;
+      o.y += base_scale * b.y;
+    }
+    vol[v] = o;
+  }
 }
 
 // Per-channel sums in FP64 over voxel blocks, then a fixed-order final sum.
@@ -394,11 +402,11 @@ rihv_status rihv_nn_pack_input(const void* vol, uint16_t* out, size_t voxels, in
   return launched();
 }
 
-rihv_status rihv_nn_unpack_output(const float* y, void* vol, size_t voxels, int c, float scale,
-                                  void* stream) {
+rihv_status rihv_nn_unpack_output(const float* y, const void* base, float base_scale, void* vol,
+                                  size_t voxels, int c, float scale, void* stream) {
   if (!y || !vol || c < 2) return RIHV_ERR_INVALID_ARG;
   k_unpack_output<<<grid_for(voxels), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      y, static_cast<float2*>(vol), voxels, c, scale);
+      y, static_cast<const float2*>(base), base_scale, static_cast<float2*>(vol), voxels, c, scale);
   return launched();
 }
 

@@ -32,7 +32,7 @@ def _lib():
             "rihv_nn_concat": (i, [vp, vp, vp, sz, i, i, vp]),
             "rihv_nn_split": (i, [vp, vp, vp, sz, i, i, vp]),
             "rihv_nn_pack_input": (i, [vp, vp, sz, i, f, vp]),
-            "rihv_nn_unpack_output": (i, [vp, vp, sz, i, f, vp]),
+            "rihv_nn_unpack_output": (i, [vp, vp, f, vp, sz, i, f, vp]),
             "rihv_nn_mse_grad": (i, [vp, vp, vp, vp, sz, i, f, vp, vp]),
             "rihv_nn_adam": (i, [vp, vp, vp, vp, vp, sz, f, f, f, f, i, vp]),
         }
@@ -125,9 +125,9 @@ def pack_input(vol, out, voxels, c, scale):
         "rihv_nn_pack_input")
 
 
-def unpack_output(y, vol, voxels, c, scale):
-    _ok(_lib().rihv_nn_unpack_output(_p(y), _p(vol), voxels, c, float(scale), _stream()),
-        "rihv_nn_unpack_output")
+def unpack_output(y, vol, voxels, c, scale, base=None, base_scale=0.0):
+    _ok(_lib().rihv_nn_unpack_output(_p(y), _p(base), float(base_scale), _p(vol), voxels, c,
+                                     float(scale), _stream()), "rihv_nn_unpack_output")
 
 
 def mse_grad(y, target, gy, loss, voxels, c, scale, work):

@@ -1,9 +1,12 @@
 """Learned warm start for FISTA: a small 3D U-Net on tcgen05 convolutions.
 
 Not in the paper. The network maps the back-propagated hologram H^H b (two
-channels: real and imaginary part) of one volume to an initial volume x0 for
-the fused-lasso FISTA solve; plain FISTA from zero remains the fallback and
-the judge of the result (the solver refines x0 to the same objective).
+channels: real and imaginary part) of one volume to an initial volume for the
+fused-lasso FISTA solve, x0 = base_coeff * H^H b + scale_out * net(H^H b): the
+first term is FISTA's own first iterate from zero (base_coeff = 2 tau), so the
+network learns the correction that FISTA would otherwise build over many
+iterations. Plain FISTA from zero remains the fallback and the judge of the
+result (the solver refines x0 to the same objective).
 
 Architecture (3 levels, 16/32/64 channels, 3x3x3 convolutions, BF16 weights
 and activations, FP32 accumulation):
@@ -60,6 +63,7 @@ class WarmStartUNet:
             self._set(name, w0, torch.zeros(cout))
         self.scale_in = 1.0
         self.scale_out = 1.0
+        self.base_coeff = 0.0
         self.step_count = 0
         self.err = torch.zeros(1, dtype=torch.int32, device=self.dev)
         self._bufs = {}
@@ -195,7 +199,8 @@ class WarmStartUNet:
         return inp
 
     def train_step(self, hb, target, lr=1e-3):
-        """One Adam step on MSE(net(hb), target / scale_out); returns the loss."""
+        """One Adam step on MSE(net(hb), target / scale_out); returns the loss.
+        target is the correction x* - base_coeff * hb."""
         out = self.forward(self.pack(hb))
         g = self._buf("gout", 0, C_IO)
         loss = self._bufs.get("loss")
@@ -209,9 +214,10 @@ class WarmStartUNet:
         return loss
 
     def predict(self, hb, x0_out):
-        """x0 = scale_out * net(scale_in * H^H b), complex64 [d][h][w]."""
+        """x0 = base_coeff * H^H b + scale_out * net(scale_in * H^H b)."""
         out = self.forward(self.pack(hb))
-        nn.unpack_output(out, x0_out, self.nv[0], C_IO, self.scale_out)
+        nn.unpack_output(out, x0_out, self.nv[0], C_IO, self.scale_out, base=hb,
+                         base_scale=self.base_coeff)
         return x0_out
 
     def state(self):
@@ -219,6 +225,7 @@ class WarmStartUNet:
         st.update({f"b_{n}": self.b[n].cpu().numpy() for n, *_ in LAYERS})
         st["scale_in"] = np.float64(self.scale_in)
         st["scale_out"] = np.float64(self.scale_out)
+        st["base_coeff"] = np.float64(self.base_coeff)
         st["dims"] = np.array(self.dims[0])
         return st
 
@@ -233,6 +240,7 @@ class WarmStartUNet:
             net._set(n, torch.from_numpy(st[f"W_{n}"]), torch.from_numpy(st[f"b_{n}"]))
         net.scale_in = float(st["scale_in"])
         net.scale_out = float(st["scale_out"])
+        net.base_coeff = float(st["base_coeff"]) if "base_coeff" in st else 0.0
         return net
 
     def errors(self):

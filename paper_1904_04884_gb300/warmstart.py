@@ -5,8 +5,9 @@ Samples are seeded synthetic particle volumes of 256 x 256 x 64 voxels
 optics of the 512x512 workload (5 um pitch, 532 nm, z0 5 mm, dz 50 um).
 Holograms come from this library's forward operator, the network input is
 the back-propagated hologram H^H b (rihv_adjoint), and the training target is
-the fused-lasso FISTA solution of that hologram (rihv_solve), so the network
-learns to predict the minimiser that FISTA then refines.
+the fused-lasso FISTA solution x* of that hologram (rihv_solve) minus FISTA's
+first iterate from zero (2 tau H^H b), so the network learns the correction
+that FISTA would otherwise build over many iterations.
 
     python -m paper_1904_04884_gb300.warmstart train --n-train 256 --epochs 8 \
         --out paper_1904_04884_gb300/weights/warmstart_256x256x64.npz
@@ -97,6 +98,9 @@ def train(n_train=256, epochs=8, lr=1e-3, seed0=1, out=DEFAULT_WEIGHTS, spec=SPE
     torch.cuda.synchronize()
     t_data = time.time() - t0
     net = WarmStartUNet((spec.nz, spec.ny, spec.nx), seed=seed0)
+    net.base_coeff = float(2.0 * h.step_size())
+    # targets: the correction to FISTA's first iterate (data preparation)
+    data = [(hb, (x - net.base_coeff * hb).contiguous()) for hb, x in data]
     k = min(16, n_train)
     net.scale_in = float(1.0 / np.mean([hb.abs().pow(2).mean().sqrt().item() for hb, _ in data[:k]]))
     net.scale_out = float(np.mean([x.abs().pow(2).mean().sqrt().item() for _, x in data[:k]]))
