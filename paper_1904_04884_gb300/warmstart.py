@@ -123,6 +123,7 @@ def train(n_train=256, epochs=8, lr=1e-3, seed0=1, out=DEFAULT_WEIGHTS, spec=SPE
     os.makedirs(os.path.dirname(out), exist_ok=True)
     net.save(out)
     info = {"n_train": n_train, "epochs": epochs, "lr": lr, "losses": losses,
+            "lam_l1": spec.lam_l1, "lam_tv": spec.lam_tv, "target_iters": spec.target_iters,
             "data_seconds": t_data, "train_seconds": t_train,
             "steps": n_train * epochs, "ms_per_step": 1e3 * t_train / (n_train * epochs)}
     with open(os.path.splitext(out)[0] + ".json", "w") as f:
@@ -184,12 +185,16 @@ def main():
     e = sub.add_parser("eval")
     e.add_argument("--weights", default=DEFAULT_WEIGHTS)
     e.add_argument("--seeds", type=int, nargs="+", default=[20001, 20002, 20003])
+    for q in (t, e):
+        q.add_argument("--lam-l1", type=float, default=SPEC.lam_l1)
+        q.add_argument("--lam-tv", type=float, default=SPEC.lam_tv)
     a = p.parse_args()
+    spec = SampleSpec(lam_l1=a.lam_l1, lam_tv=a.lam_tv)
     if a.cmd == "train":
-        _, info = train(a.n_train, a.epochs, a.lr, out=a.out)
+        _, info = train(a.n_train, a.epochs, a.lr, out=a.out, spec=spec)
         print(json.dumps(info))
     else:
-        print(json.dumps(evaluate(a.weights, a.seeds)))
+        print(json.dumps(evaluate(a.weights, a.seeds, spec=spec)))
 
 
 if __name__ == "__main__":
