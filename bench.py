@@ -12,6 +12,8 @@ roofline: the TV dual-step kernel (the dominant kernel), from CUDA events the
          steps; algorithmic bytes 32 (first step) + 56 per later step per voxel.
 cpu_baseline: the FP64 oracle on a bounded sample (two FISTA iterations on a
          16-plane slab of the same workload), host cores.
+time_to_tolerance: per-hologram time to F*(1+1e-3) on held-out 256x256x64
+         samples, plain FISTA vs the learned warm start + batched CUDA graph.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank reconstructs its own hologram (independent work, no
@@ -44,6 +46,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-warmstart", action="store_true",
+                   help="skip the time-to-tolerance comparison (plain vs warm start + batched)")
     return p.parse_args()
 
 
@@ -158,6 +162,59 @@ def cpu_baseline_sample(w, iters=2, planes=16):
     O.fista(b.astype(np.float64), op, w.lam_l1, w.lam_tv, iters, w.n_inner)
     dt = time.perf_counter() - t0
     return w.nx * w.ny * planes * iters / dt, dt
+
+
+def time_to_tolerance(seeds=(20001, 20002, 20003, 20004), tol=1e-3):
+    """Per-hologram wall time to reach F* (1 + tol) on held-out 256x256x64
+    samples: plain FISTA from zero (stop test every 10 iterations) against the
+    learned warm start plus all holograms solved together as one batched CUDA
+    graph for the warm iteration count measured beforehand (the larger one of
+    the batch). F* is the objective of a 600-iteration plain solve."""
+    import torch
+    from paper_1904_04884_gb300 import warmstart as W
+    from paper_1904_04884_gb300.rihv import Batch
+    from paper_1904_04884_gb300.unet import WarmStartUNet
+
+    dev = torch.device("cuda:0")
+    spec = W.SPEC
+    net = WarmStartUNet.load(W.DEFAULT_WEIGHTS)
+    h = W.handle(spec)
+    samples = [W.make_sample(h, spec, s, dev) for s in seeds]
+    f_star = [W.reference_objective(h, b, spec) for b, _ in samples]
+    plain_t, plain_it, warm_it = [], [], []
+    for (b, hb), fs in zip(samples, f_star):
+        it, t, _ = W.iterations_to_tolerance(h, b, spec, None, fs, tol)
+        plain_it.append(it)
+        plain_t.append(t)
+        x0 = torch.empty(spec.shape, dtype=torch.complex64, device=dev)
+        net.predict(hb, x0)
+        it, _, _ = W.iterations_to_tolerance(h, b, spec, x0, fs, tol)
+        warm_it.append(it)
+    hs = [W.handle(spec) for _ in seeds]
+    batch = Batch(hs)
+    iters = max(warm_it)
+    x0s = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in seeds]
+    outs = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in seeds]
+
+    def warm_batched():
+        for (b, hb), x0 in zip(samples, x0s):
+            net.predict(hb, x0)
+        batch.solve([b for b, _ in samples], spec.lam_l1, spec.lam_tv, iters, outs, x0s=x0s)
+        torch.cuda.synchronize()
+
+    warm_batched()                       # capture the graph
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        warm_batched()
+    t_wb = (time.perf_counter() - t0) / reps / len(seeds)
+    batch.close()
+    t_plain = float(np.mean(plain_t))
+    return {"workload": "warmstart_256x256x64 (lambda 0.01 / 0.005, K = 20)",
+            "tolerance": tol, "seeds": list(seeds), "plain_iters": plain_it,
+            "warm_iters": warm_it, "batched_iters": iters,
+            "plain_s_per_hologram": t_plain, "warm_batched_s_per_hologram": t_wb,
+            "speedup": t_plain / t_wb}
 
 
 def run_reference(args, rank, world):
@@ -303,6 +360,10 @@ def main():
     peak, peak_kind = hbm_peak()
     total_launches = sum(n for _, n in stages.values())
 
+    ttt = None
+    if not args.no_warmstart:
+        ttt = time_to_tolerance()
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, dt = cpu_baseline_sample(w)
@@ -331,6 +392,7 @@ def main():
                      "alg_bytes_per_launch": alg_bytes_per_launch,
                      "avg_launch_ms": avg_launch_s * 1e3},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "time_to_tolerance": ttt,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
