@@ -2,7 +2,8 @@
 profilers (ncu) and quick timing.
 
 python -m paper_1904_04884_gb300.profile_ops --op prox --nx 256 --ny 256 --nz 64 --reps 3
-ops: forward, adjoint, prox (fused-lasso prox with --inner TV steps), solve.
+ops: forward, adjoint, prox (fused-lasso prox with --inner TV steps), solve,
+unet (warm-start network inference), unet_train (one training step).
 """
 from __future__ import annotations
 
@@ -14,7 +15,8 @@ import numpy as np
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--op", default="prox", choices=["forward", "adjoint", "prox", "solve"])
+    p.add_argument("--op", default="prox",
+                   choices=["forward", "adjoint", "prox", "solve", "unet", "unet_train"])
     p.add_argument("--nx", type=int, default=256)
     p.add_argument("--ny", type=int, default=256)
     p.add_argument("--nz", type=int, default=64)
@@ -36,8 +38,17 @@ def main():
     plane = torch.empty((a.ny, a.nx), dtype=torch.complex64, device=dev)
     holo = torch.from_numpy(np.ones((a.ny, a.nx), np.float32)).to(dev)
 
+    net = None
+    if a.op.startswith("unet"):
+        from paper_1904_04884_gb300.unet import WarmStartUNet
+        net = WarmStartUNet((a.nz, a.ny, a.nx), seed=0)
+
     def once():
-        if a.op == "forward":
+        if a.op == "unet":
+            net.predict(vol, out)
+        elif a.op == "unet_train":
+            net.train_step(vol, out)
+        elif a.op == "forward":
             h.forward(vol, plane)
         elif a.op == "adjoint":
             h.adjoint(plane, out)
