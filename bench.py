@@ -118,14 +118,14 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(nvox):
-    """DRAM bytes per TV-step launch from the committed ncu summary, scaled to
-    this workload, or None when the kernel changed since it was captured."""
+def measured_traffic(nvox, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to this workload, or None when the kernel changed since it was captured."""
     try:
         prof = json.load(open(TV_PROFILE))
     except Exception:
         return None
-    if prof.get("kernel_hash") != kernel_hash():
+    if prof.get("kernel_hash") != kernel_hash() or prof.get("kernel_name") != kernel:
         return None
     return prof["dram_bytes_per_voxel_per_launch"] * nvox
 
@@ -348,7 +348,8 @@ def main():
     value = vox_iters * args.steps * world / (ms / 1e3)
     e2e_value = vox_iters * e2e_steps * world / (e2e_ms / 1e3)
 
-    # roofline of the TV dual step, from the live stage events
+    # roofline of the TV dual-step kernel, from the live stage events
+    tv_kernel = "k_tv_step2" if h.options.tv_steps_per_launch == 2 else "k_tv_step"
     tv_ms, tv_launches = stages["tv"]
     # 32 B/voxel for the launch that starts from p = 0 (reads v, writes p),
     # 56 B/voxel for every other launch (reads v and p, writes p), whatever
@@ -385,11 +386,12 @@ def main():
                 "h2d_bytes_per_step": int(w.nx * w.ny * 4),
                 "d2h_bytes_per_step": int(w.nvox * 8 + (w.iters // 10) * 8)},
         "gpu_launches": int(total_launches),
-        "roofline": {"bound": "hbm", "kernel": "k_tv_step", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": tv_kernel, "achieved": achieved,
                      "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": measured_traffic(w.nvox), "peak_kind": peak_kind,
+                     "traffic": measured_traffic(w.nvox, tv_kernel), "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes_per_launch,
+                     "dual_steps_per_launch": h.options.tv_steps_per_launch,
                      "avg_launch_ms": avg_launch_s * 1e3},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "time_to_tolerance": ttt,

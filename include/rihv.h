@@ -57,7 +57,7 @@ typedef enum {
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
- * tv_steps_per_launch 1. */
+ * tv_steps_per_launch 2. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -68,8 +68,10 @@ typedef struct {
   double tol;        /* with f_star > 0: stop at the first check where       */
   double f_star;     /*   F(x_k) <= f_star * (1 + tol)                       */
   int tv_steps_per_launch; /* 1: one dual step per kernel launch; 2: two
-                        steps per launch (same arithmetic, scheduled with
-                        the first step recomputed on a shared-memory halo)   */
+                        steps per launch (same arithmetic, the first step
+                        recomputed on a one-voxel halo ring; an odd step
+                        count ends with a one-step launch). 2 needs nx even,
+                        which every supported size is.                       */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */
@@ -171,7 +173,7 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
 rihv_status rihv_batch_destroy(rihv_batch b);
 
 /* Autotuner (not in the paper). Times, on the handle's own scratch, the TV
- * kernel's z-chunk length (8..128 planes per CTA) and steps per launch (1 or
+ * kernel's z-chunk length (8..256 planes per CTA) and steps per launch (1 or
  * 2, i.e. halo depth), and the number of planes each column-pass CTA sums
  * (z-group size), then applies the fastest to the handle. With a non-NULL
  * cache_path the result is looked up first (key: nx ny nz tv_dims) and
@@ -186,9 +188,9 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_
  * memory only from their own fixed arena, and services that stop allocating
  * after start-up so that no request fails for lack of memory.
  *
- * It computes exactly what rihv_prox_fused_lasso computes (tv_dims TV prox by
- * inner_iters dual gradient-projection steps from p = 0, then soft threshold
- * with t_l1), without a handle. Its scratch (the dual variable) is a static
+ * It computes what rihv_prox_fused_lasso computes, up to FP32 rounding order
+ * (tv_dims TV prox by inner_iters dual gradient-projection steps from p = 0,
+ * then soft threshold with t_l1), without a handle. Its scratch (the dual variable) is a static
  * device array inside the library of 6 x 8 MiB + 256 B, reserved on every GPU
  * that loads the library until the process exits. Limits: nx even and >= 2,
  * ny, nz >= 1, nx*ny*nz <= 1,048,576 voxels; larger volumes return

@@ -105,12 +105,12 @@ extern "C" rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out,
   float2* const* pfinal = nullptr;
   if (tv) {
     TvArgs a{};
-    if (make_volume_tmap(&a.tm_v, v, nx, ny, nz, kTvBoxH1) != cudaSuccess)
+    if (make_volume_tmap(&a.tm_v, v, nx, ny, nz, kTvBoxH1, kTvBoxW) != cudaSuccess)
       return fail(RIHV_ERR_CUDA, "tensor map encoding failed");
     CUtensorMap tma[3], tmb[3];
     for (int c = 0; c < 3; ++c)
-      if (make_volume_tmap(&tma[c], pa[c], nx, ny, nz, kTvBoxH1) != cudaSuccess ||
-          make_volume_tmap(&tmb[c], pb[c], nx, ny, nz, kTvBoxH1) != cudaSuccess)
+      if (make_volume_tmap(&tma[c], pa[c], nx, ny, nz, kTvBoxH1, kTvBoxW) != cudaSuccess ||
+          make_volume_tmap(&tmb[c], pb[c], nx, ny, nz, kTvBoxH1, kTvBoxW) != cudaSuccess)
         return fail(RIHV_ERR_CUDA, "tensor map encoding failed");
     a.err = err;
     a.nx = nx;

@@ -71,7 +71,7 @@ struct rihv_ctx {
   int device = 0;
   int groups = 1, zpg = 1;
   int sms = 152;
-  int tv_zchunk = 32;
+  int tv_zchunk = 0;                 // planes per TV z-chunk; 0: tv_default_zchunk
   double tau = 0;
   FftPlan plan_x{}, plan_y{};
   std::string err;
@@ -290,15 +290,15 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   const int launches = per == 2 ? k / 2 + (k % 2) : k;
   StageScope sc(h, ST_TV, launches);
   CUtensorMap tm_v[2];
-  CK(make_volume_tmap(&tm_v[0], v, h->nx, h->ny, h->nz, kTvBoxH1));
-  if (per == 2) CK(make_volume_tmap(&tm_v[1], v, h->nx, h->ny, h->nz, kTvBoxH2));
+  CK(make_volume_tmap(&tm_v[0], v, h->nx, h->ny, h->nz, kTvBoxH1, kTvBoxW));
+  if (per == 2) CK(make_volume_tmap(&tm_v[1], v, h->nx, h->ny, h->nz, kTv2BoxH, kTv2BoxW));
   TvArgs a{};
   a.err = h->tv_err;
   a.nx = h->nx;
   a.ny = h->ny;
   a.nz = h->nz;
   a.dims = h->opt.tv_dims;
-  a.zchunk = h->tv_zchunk;
+  const int zc_auto = tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
   a.mu = mu;
   a.step = 1.f / (4.f * a.dims * mu);
   float2** src = h->pb;
@@ -308,6 +308,7 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   while (done < k) {
     const int n = (per == 2 && k - done >= 2) ? 2 : 1;
     const int b = n == 2 ? 1 : 0;
+    a.zchunk = h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32);
     a.tm_v = tm_v[b];
     for (int c = 0; c < 3; ++c) {
       a.tm_p[c] = src_is_b ? h->tm_pb[b][c] : h->tm_pa[b][c];
@@ -456,7 +457,7 @@ void rihv_default_options(rihv_options* o) {
   o->check_every = 10;
   o->tol = 0.0;
   o->f_star = 0.0;
-  o->tv_steps_per_launch = 1;
+  o->tv_steps_per_launch = 2;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -527,9 +528,10 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
     return cleanup(fail(h, RIHV_ERR_CUDA, "memset failed"));
   for (int b = 0; b < 2; ++b)
     for (int c = 0; c < 3; ++c) {
-      const int rows = b == 0 ? kTvBoxH1 : kTvBoxH2;
-      if (make_volume_tmap(&h->tm_pa[b][c], h->pa[c], nx, ny, nz, rows) != cudaSuccess ||
-          make_volume_tmap(&h->tm_pb[b][c], h->pb[c], nx, ny, nz, rows) != cudaSuccess)
+      const int rows = b == 0 ? kTvBoxH1 : kTv2BoxH;
+      const int cols = b == 0 ? kTvBoxW : kTv2BoxW;
+      if (make_volume_tmap(&h->tm_pa[b][c], h->pa[c], nx, ny, nz, rows, cols) != cudaSuccess ||
+          make_volume_tmap(&h->tm_pb[b][c], h->pb[c], nx, ny, nz, rows, cols) != cudaSuccess)
         return cleanup(fail(h, RIHV_ERR_CUDA, "tensor map encoding failed"));
     }
 
@@ -1025,7 +1027,7 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     double best = 1e30;
     const int kSteps = 4;
     for (int p = 1; p <= 2; ++p) {
-      for (int zc : {8, 16, 32, 64, 128}) {
+      for (int zc : {8, 16, 32, 64, 128, 256}) {
         if (zc > h->nz && zc != 8) continue;
         h->opt.tv_steps_per_launch = p;
         h->tv_zchunk = zc;

@@ -26,8 +26,17 @@ constexpr int kTvTy = 8;           // TV tile height (y)
 constexpr int kTvThreads = kTvTx * kTvTy;
 constexpr int kTvBoxW = kTvTx + 4;  // TMA box width in complex elements (x from i0-2)
 constexpr int kTvBoxH1 = kTvTy + 2; // box height, one step per launch (y from j0-1)
-constexpr int kTvBoxH2 = kTvTy + 4; // box height, two steps per launch (y from j0-2)
 constexpr int kTvStages = 4;        // planes in the shared-memory ring
+// Two steps per launch: a 60 x 16 output tile; one warp per row of the 19-row
+// halo (y from j0-1), each lane two x positions (x from i0-2); box 64 x 20 from
+// (i0-2, j0-2); a 3-stage plane ring; one CTA per SM.
+constexpr int kTv2Tx = 60;
+constexpr int kTv2Ty = 16;
+constexpr int kTv2Warps = kTv2Ty + 3;
+constexpr int kTv2Threads = 32 * kTv2Warps;
+constexpr int kTv2BoxW = kTv2Tx + 4;
+constexpr int kTv2BoxH = kTv2Ty + 4;
+constexpr int kTv2Stages = 3;
 
 constexpr int kRedBlocks = 1216;   // fixed grid of the streaming reduction kernels (8 x 152)
 constexpr int kRedThreads = 256;
@@ -115,9 +124,12 @@ struct TvArgs {
 };
 // nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero.
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s);
-// box_rows: kTvBoxH1 for the one-step kernel, kTvBoxH2 for the two-step one.
+// Planes per z-chunk of the TV launch grid when none was tuned.
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms);
+// Box of box_rows x box_cols complex elements: (kTvBoxH1, kTvBoxW) for the
+// one-step kernel, (kTv2BoxH, kTv2BoxW) for the two-step kernel.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
-                             int box_rows);
+                             int box_rows, int box_cols);
 
 enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };
 struct FinArgs {

@@ -14,8 +14,8 @@
 // stencil's halo, with the x start kept on a 16-byte boundary; out-of-range
 // boxes are zero filled) into a 4-stage ring completed by mbarriers, so two planes are in flight while one is
 // computed. k_tv_step2 performs two dual steps per launch (temporal blocking,
-// first step recomputed on a halo ring in shared memory); k_tv_step performs
-// one (for odd step counts). Outputs go out with plain coalesced stores. Every
+// first step recomputed on a one-voxel halo ring, one warp per tile row);
+// k_tv_step performs one (for odd step counts). Outputs go out with plain coalesced stores. Every
 // wait is bounded: on timeout the CTA sets the error flag, drains its copies
 // in flight and exits.
 //
@@ -36,13 +36,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 
 constexpr int TX = kTvTx;
 constexpr int TY = kTvTy;
-constexpr int BW = kTvBoxW;       // TMA box: complex x in [i0-2, i0+TX+2)
-constexpr int BH1 = kTvBoxH1;     //   one step:  y in [j0-1, j0+TY+1)
-constexpr int BH2 = kTvBoxH2;     //   two steps: y in [j0-2, j0+TY+2)
+constexpr int BW = kTvBoxW;       // one-step TMA box: complex x in [i0-2, i0+TX+2)
+constexpr int BH1 = kTvBoxH1;     //                   y in [j0-1, j0+TY+1)
 constexpr int NSTAGE = kTvStages;
-constexpr int slot_bytes(int bh) { return ((BW * bh * 8 + 127) / 128) * 128; }
-constexpr int SLOT1 = slot_bytes(BH1);
-constexpr int SLOT2 = slot_bytes(BH2);
+constexpr int slot_bytes(int bw, int bh) { return ((bw * bh * 8 + 127) / 128) * 128; }
+constexpr int SLOT1 = slot_bytes(BW, BH1);
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
 
 // Regions (x extent, y extent) relative to the tile origin (i0, j0):
@@ -103,31 +101,35 @@ __device__ __forceinline__ void project(float2& qx, float2& qy, float2& qz) {
   }
 }
 
-// Plane ring fed by TMA: NSTAGE stages x 4 slots (v, p_x, p_y, p_z) of a
-// BH-row box each. Plane q lives in stage (q - base) mod NSTAGE; its n-th use
+// Plane ring fed by TMA: NS stages x 4 slots (v, p_x, p_y, p_z) of a
+// BH x BWR box each. Plane q lives in stage (q - base) mod NS; its n-th use
 // has mbarrier parity n&1.
-template <int BH>
+template <int BWR, int BH, int Y0, int NS>
 struct PlaneRing {
-  static constexpr int kSlot = slot_bytes(BH);
-  static constexpr int kY0 = (BH - TY) / 2;   // box row of the tile's first row
+  static constexpr int kSlot = slot_bytes(BWR, BH);
+  static constexpr int kW = BWR;
+  static constexpr int kH = BH;
+  static constexpr int kY0 = Y0;   // box row of the tile's first row
+  static constexpr int kStages = NS;
   unsigned char* smem;
   unsigned long long* bars;
-  int base;
-  __device__ float2 (*slot(int q, int arr) const)[BW] {
-    const int s = (q - base) & (NSTAGE - 1);
-    return reinterpret_cast<float2(*)[BW]>(smem + (s * 4 + arr) * kSlot);
+  int base;                        // first plane of the ring (q - base >= 0)
+  __device__ int stage(int q) const { return static_cast<int>(static_cast<unsigned>(q - base) % NS); }
+  __device__ float2 (*slot(int q, int arr) const)[BWR] {
+    return reinterpret_cast<float2(*)[BWR]>(smem + (stage(q) * 4 + arr) * kSlot);
   }
-  __device__ unsigned bar(int q) const { return smem_addr(&bars[(q - base) & (NSTAGE - 1)]); }
-  __device__ unsigned parity(int q) const { return static_cast<unsigned>(((q - base) / NSTAGE) & 1); }
+  __device__ unsigned bar(int q) const { return smem_addr(&bars[stage(q)]); }
+  __device__ unsigned parity(int q) const {
+    return (static_cast<unsigned>(q - base) / NS) & 1u;
+  }
 };
 
-template <bool FIRST, int BH>
-__device__ __forceinline__ void ring_issue(const PlaneRing<BH>& r, const TvArgs& a, int q, int i0,
-                                           int j0) {
+template <bool FIRST, class Ring>
+__device__ __forceinline__ void ring_issue(const Ring& r, const TvArgs& a, int q, int i0, int j0) {
   const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
   const unsigned bar = r.bar(q);
-  mbar_expect_tx(bar, static_cast<unsigned>(nslots * BW * BH * 8));
-  const int x = 2 * (i0 - 2), y = j0 - PlaneRing<BH>::kY0;
+  mbar_expect_tx(bar, static_cast<unsigned>(nslots * Ring::kW * Ring::kH * 8));
+  const int x = 2 * (i0 - 2), y = j0 - Ring::kY0;
   tma_load_3d(smem_addr(r.slot(q, 0)), &a.tm_v, x, y, q, bar);
   if (!FIRST) {
     tma_load_3d(smem_addr(r.slot(q, 1)), &a.tm_p[0], x, y, q, bar);
@@ -137,16 +139,16 @@ __device__ __forceinline__ void ring_issue(const PlaneRing<BH>& r, const TvArgs&
 }
 
 // Block-uniform bounded wait for plane q.
-template <int BH>
-__device__ __forceinline__ bool ring_wait(const PlaneRing<BH>& r, int q) {
+template <class Ring>
+__device__ __forceinline__ bool ring_wait(const Ring& r, int q) {
   const bool ok = mbar_wait(r.bar(q), r.parity(q));
   return __syncthreads_and(ok) != 0;
 }
 
 // Records a failed wait and drains this CTA's copies in flight (bounded)
 // before its shared memory is released.
-template <int BH>
-__device__ __forceinline__ void ring_abort(const PlaneRing<BH>& r, const TvArgs& a, int waited,
+template <class Ring>
+__device__ __forceinline__ void ring_abort(const Ring& r, const TvArgs& a, int waited,
                                            int issued) {
   if (threadIdx.x == 0) {
     atomicExch(a.err, 1);
@@ -189,8 +191,8 @@ template <bool FIRST>
 __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ TvArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float2(*U)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + NSTAGE * 4 * SLOT1);
-  PlaneRing<BH1> ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout1::kBarOffset),
-                      static_cast<int>(blockIdx.z) * a.zchunk - 1};
+  PlaneRing<BW, BH1, 1, NSTAGE> ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout1::kBarOffset),
+                             static_cast<int>(blockIdx.z) * a.zchunk - 1};
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
@@ -268,163 +270,289 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
   }
 }
 
+constexpr int TX2 = kTv2Tx;
+constexpr int NW2 = kTv2Warps;
+constexpr int SLOT2 = slot_bytes(kTv2BoxW, kTv2BoxH);
+using Ring2 = PlaneRing<kTv2BoxW, kTv2BoxH, 2, kTv2Stages>;
+
 struct TvLayout2 {   // two dual steps per launch
-  static constexpr int kU0Off = NSTAGE * 4 * SLOT2;
-  static constexpr int kU0Bytes = 2 * AY * AX * 8;
-  static constexpr int kP1Off = kU0Off + kU0Bytes;
-  static constexpr int kP1Bytes = 2 * 3 * R2Y * R2X * 8;
-  static constexpr int kU1Off = kP1Off + kP1Bytes;
-  static constexpr int kU1Bytes = 2 * R1Y * R1X * 8;
-  static constexpr int kBarOffset = kU1Off + kU1Bytes;
-  static constexpr int kBytes = kBarOffset + NSTAGE * 8;
+  static constexpr int kXOff = kTv2Stages * 4 * SLOT2;
+  // exchange rows for y-neighbours (one pair of complex values per lane),
+  // double buffered by plane parity: u0 [2][NW2][32], p1_y [2][NW2][32], u1 [2][NW2][32]
+  static constexpr int kXRow = NW2 * 32 * 16;
+  static constexpr int kBarOffset = kXOff + 6 * kXRow;
+  static constexpr int kBytes = kBarOffset + kTv2Stages * 8;
 };
 
+// Packed two-lane FP32 arithmetic (f32x2, sm_100 and later) on complex
+// values: one instruction per complex add, subtract, multiply-add or scale,
+// each lane rounded as the scalar instruction would.
+__device__ __forceinline__ unsigned long long as_b64(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 as_f2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 x2add(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_b64(a)), "l"(as_b64(b)));
+  return as_f2(d);
+}
+__device__ __forceinline__ float2 x2sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_b64(a)), "l"(as_b64(b)));
+  return as_f2(d);
+}
+__device__ __forceinline__ float2 x2mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_b64(a)), "l"(as_b64(b)));
+  return as_f2(d);
+}
+// a * b + c, lane by lane, one rounding
+__device__ __forceinline__ float2 x2fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_b64(a)), "l"(as_b64(b)), "l"(as_b64(c)));
+  return as_f2(d);
+}
+// Projection onto the unit ball of C^3 with packed arithmetic, branch free
+// (a scale of 1 leaves the vector unchanged).
+__device__ __forceinline__ void project2(float2& qx, float2& qy, float2& qz) {
+  const float2 s = x2fma(qz, qz, x2fma(qy, qy, x2mul(qx, qx)));
+  const float n2 = s.x + s.y;
+  const float r = n2 > 1.f ? rsqrtf(n2) : 1.f;
+  const float2 sc = make_float2(r, r);
+  qx = x2mul(qx, sc);
+  qy = x2mul(qy, sc);
+  qz = x2mul(qz, sc);
+}
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 pack4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
 // Two dual gradient-projection steps per launch (temporal blocking). With p^0
-// the input dual and p^2 the output, per plane tick t of the z march:
-//   (a) u^0(t+1) over A   from p^0(t+1), p^0_z(t), v(t+1)   [TMA ring]
-//   (b) p^1(t)   over R2  from u^0(t), u^0(t+1), p^0(t)
-//   (c) u^1(t)   over R1  from p^1(t), p^1_z(t-1), v(t)
-//   (d) p^2(t-1) over T   from u^1(t-1), u^1(t), p^1(t-1)   -> global
-// Step 1 is recomputed on a one-voxel halo ring around the tile (R2), which
-// needs a two-voxel halo of p^0 and v: the TMA box covers x in [i0-2, i0+TX+2)
-// and y in [j0-2, j0+TY+2). HBM traffic per voxel for two steps is one read of
-// v and p^0 and one write of p^2.
+// the input dual and p^2 the output, a 60 x 16 tile marches through its chunk
+// of planes. Thread (warp w, lane l) owns the two positions x = i0-2+2l+e
+// (e = 0, 1), y = j0-1+w of the halo (19 rows x 64 columns) and, per plane
+// tick t, computes
+//   (a) u^0(t+1) = v - mu D^H p^0              [staged box of plane t+1]
+//   (b) p^1(t)   = Pi(p^0 + step D u^0)        [u^0(t), u^0(t+1)]
+//   (c) u^1(t)   = v - mu D^H p^1              [p^1(t), p^1_z(t-1)]
+//   (d) p^2(t-1) = Pi(p^1 + step D u^1)        [u^1(t-1), u^1(t)] -> global
+// z-neighbours stay in registers across ticks; x-neighbours are the thread's
+// other position, or the neighbouring lane's (a shuffle or the exchange row);
+// y-neighbours pass through shared-memory exchange rows, double buffered by
+// plane parity. One barrier per tick, between (b) and (c), orders every
+// exchange: a row written before barrier k is read after it and rewritten
+// only after barrier k+1; it also carries the vote on the ring wait. Step 1
+// is recomputed on the halo ring, so each voxel's v and p^0 are read from HBM
+// about once and p^2 written once for two steps. Positions outside a step's
+// region compute values that no output uses; every use is guarded by the same
+// global-index boundary conditions as the single step. Needs nx even (pairs
+// of outputs are stored as 16-byte words).
 template <bool FIRST>
-__global__ void __launch_bounds__(kTvThreads, 2) k_tv_step2(const __grid_constant__ TvArgs a) {
+__global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_constant__ TvArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float2(*U0)[AY][AX] = reinterpret_cast<float2(*)[AY][AX]>(smem + TvLayout2::kU0Off);
-  float2(*P1)[3][R2Y][R2X] = reinterpret_cast<float2(*)[3][R2Y][R2X]>(smem + TvLayout2::kP1Off);
-  float2(*U1)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + TvLayout2::kU1Off);
+  using Row = float4[NW2][32];
+  using Box4 = const float4(*)[kTv2BoxW / 2];
+  Row* XU0 = reinterpret_cast<Row*>(smem + TvLayout2::kXOff);
+  Row* XP1 = XU0 + 2;
+  Row* XU1 = XU0 + 4;
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
-  // planes zc0-2 .. zc1+1 are read (out-of-range planes arrive zero filled)
-  PlaneRing<BH2> ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset),
-                      zc0 - 2};
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int tid = threadIdx.x;
+  Ring2 ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset), zc0 - 2};
+  const int i0 = blockIdx.x * TX2, j0 = blockIdx.y * kTv2Ty;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int gx0 = i0 - 2 + 2 * lane, gy = j0 - 1 + w;   // element e at x = gx0 + e
+  const int by = w + 1;                                 // own row in the box
+  const int cm = lane > 0 ? 2 * lane - 1 : 0;           // box column x-1 of element 0
+  const int ln = lane < 31 ? lane + 1 : lane;           // next lane (x+1 of element 1)
   const int qlast = zc1 + 1;
+  const bool out_pair = w >= 1 && w <= kTv2Ty && lane >= 1 && lane <= TX2 / 2 && gx0 < a.nx &&
+                        gy < a.ny;
+  const int wn = w + 1 < NW2 ? w + 1 : w;       // y+1 row (the last row's value is unused)
+  const int wp = w >= 1 ? w - 1 : w;            // y-1 row (the first row's value is unused)
+  // Boundary conditions as multipliers, so that every term is one packed
+  // multiply-add: m_lo = 1 where the backward neighbour exists (D^H term
+  // +p(x-1)), m_hi = -1 where the forward difference exists (D^H term -p(x)),
+  // s_hi = step there (the step's D u term); 0 elsewhere. Adding or
+  // subtracting through an exact +-1 or 0 multiplier rounds as the add itself.
+  // With gx0 and nx even, element 0 always has a forward neighbour and
+  // element 1 a backward one inside the volume; the exceptions lie outside it
+  // (x = -1, x >= nx), where values are computed but never used.
+  const float2 mxlo0 = splat(gx0 >= 1 ? 1.f : 0.f);
+  const float2 mxhi1 = splat(gx0 + 1 <= a.nx - 2 ? -1.f : 0.f);
+  const float2 sxhi1 = splat(gx0 + 1 <= a.nx - 2 ? a.step : 0.f);
+  const float2 stp = splat(a.step);
+  const float2 mylo = splat(gy >= 1 ? 1.f : 0.f);
+  const float2 myhi = splat(gy <= a.ny - 2 ? -1.f : 0.f);
+  const float2 syhi = splat(gy <= a.ny - 2 ? a.step : 0.f);
+  const float2 nmu = splat(-a.mu);
 
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
+    for (int s = 0; s < kTv2Stages; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   if (tid == 0)
-    for (int q = ring.base; q < ring.base + NSTAGE && q <= qlast; ++q) ring_issue<FIRST>(ring, a, q, i0, j0);
-  int issued = min(ring.base + NSTAGE - 1, qlast);
+    for (int q = ring.base; q < ring.base + kTv2Stages && q <= qlast; ++q)
+      ring_issue<FIRST>(ring, a, q, i0, j0);
+  int issued = min(ring.base + kTv2Stages - 1, qlast);
   int waited = ring.base - 1;
 
-  // (a) u^0(q) over A (box coordinates: A origin is box (1, 1))
-  auto step_a = [&](int q) {
-    float2(*u)[AX] = U0[q & 1];
-    for (int e = tid; e < AY * AX; e += kTvThreads) {
-      const int ry = e / AX, rx = e - ry * AX;
-      u[ry][rx] = u_from_box<FIRST>(a, ring.slot(q, 0), ring.slot(q, 1), ring.slot(q, 2),
-                                    ring.slot(q, 3), ring.slot(q - 1, 3), ry + 1, rx + 1,
-                                    i0 - 1 + rx, j0 - 1 + ry, q);
-    }
-  };
-  // (b) p^1(q) over R2 (R2 origin is A (0, 0) and box (1, 1))
-  auto step_b = [&](int q) {
-    float2(*u)[AX] = U0[q & 1];
-    float2(*un)[AX] = U0[(q + 1) & 1];
-    float2(*p1)[R2Y][R2X] = P1[q & 1];
-    for (int e = tid; e < R2Y * R2X; e += kTvThreads) {
-      const int ry = e / R2X, rx = e - ry * R2X;
-      const int gx = i0 - 1 + rx, gy = j0 - 1 + ry;
-      const float2 u0 = u[ry][rx];
-      float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
-      if (gx <= a.nx - 2) dx = csub(u[ry][rx + 1], u0);
-      if (gy <= a.ny - 2) dy = csub(u[ry + 1][rx], u0);
-      if (a.dims == 3 && q <= a.nz - 2) dz = csub(un[ry][rx], u0);
-      float2 qx = make_float2(0.f, 0.f), qy = qx, qz = qx;
-      if (!FIRST) {
-        qx = ring.slot(q, 1)[ry + 1][rx + 1];
-        qy = ring.slot(q, 2)[ry + 1][rx + 1];
-        if (a.dims == 3) qz = ring.slot(q, 3)[ry + 1][rx + 1];
-      }
-      qx = fma2(qx, a.step, dx);
-      qy = fma2(qy, a.step, dy);
-      qz = fma2(qz, a.step, dz);
-      project(qx, qy, qz);
-      p1[0][ry][rx] = qx;
-      p1[1][ry][rx] = qy;
-      p1[2][ry][rx] = qz;
-    }
-  };
-  // (c) u^1(q) over R1 (R1 origin is R2 (1, 1) and box (2, 2))
-  auto step_c = [&](int q) {
-    float2(*p1)[R2Y][R2X] = P1[q & 1];
-    float2(*p1m)[R2Y][R2X] = P1[(q + 1) & 1];   // plane q-1
-    float2(*vs)[BW] = ring.slot(q, 0);
-    float2(*u)[R1X] = U1[q & 1];
-    for (int e = tid; e < R1Y * R1X; e += kTvThreads) {
-      const int ry = e / R1X, rx = e - ry * R1X;
-      const int gx = i0 + rx, gy = j0 + ry;
-      float2 dh = make_float2(0.f, 0.f);
-      if (gx >= 1) dh = cadd(dh, p1[0][ry + 1][rx]);
-      if (gx <= a.nx - 2) dh = csub(dh, p1[0][ry + 1][rx + 1]);
-      if (gy >= 1) dh = cadd(dh, p1[1][ry][rx + 1]);
-      if (gy <= a.ny - 2) dh = csub(dh, p1[1][ry + 1][rx + 1]);
-      if (a.dims == 3) {
-        if (q >= 1) dh = cadd(dh, p1m[2][ry + 1][rx + 1]);
-        if (q <= a.nz - 2) dh = csub(dh, p1[2][ry + 1][rx + 1]);
-      }
-      const float2 v = vs[ry + 2][rx + 2];
-      u[ry][rx] = make_float2(v.x - a.mu * dh.x, v.y - a.mu * dh.y);
-    }
-  };
-  // (d) p^2(q) over the tile -> global
-  auto step_d = [&](int q) {
-    const int tx = tid % TX, ty = tid / TX;
-    const int gi = i0 + tx, gj = j0 + ty;
-    if (gi >= a.nx || gj >= a.ny) return;
-    float2(*u)[R1X] = U1[q & 1];
-    float2(*un)[R1X] = U1[(q + 1) & 1];
-    float2(*p1)[R2Y][R2X] = P1[q & 1];
-    const float2 u0 = u[ty][tx];
-    float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
-    if (gi <= a.nx - 2) dx = csub(u[ty][tx + 1], u0);
-    if (gj <= a.ny - 2) dy = csub(u[ty + 1][tx], u0);
-    if (a.dims == 3 && q <= a.nz - 2) dz = csub(un[ty][tx], u0);
-    float2 qx = fma2(p1[0][ty + 1][tx + 1], a.step, dx);
-    float2 qy = fma2(p1[1][ty + 1][tx + 1], a.step, dy);
-    float2 qz = fma2(p1[2][ty + 1][tx + 1], a.step, dz);
-    project(qx, qy, qz);
-    const size_t gidx = (static_cast<size_t>(q) * a.ny + gj) * a.nx + gi;
-    a.pout[0][gidx] = qx;
-    a.pout[1][gidx] = qy;
-    if (a.dims == 3) a.pout[2][gidx] = qz;
-  };
+  const float2 zero = make_float2(0.f, 0.f);
+  // per-position state of plane t (index e = element)
+  float2 u0_t[2] = {zero, zero}, v_t[2] = {zero, zero};
+  float2 p0_t[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};
+  float2 p1_prev[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};
+  float2 p1_t[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};
+  float2 u1_prev[2] = {zero, zero}, u1_t[2] = {zero, zero};
 
-  // pre-tick: u^0(zc0-1) needs planes zc0-2 (p_z) and zc0-1
+  // prologue: p^0_z of plane zc0-2 (read by u^0(zc0-1))
   if (!ring_wait(ring, zc0 - 2)) { ring_abort(ring, a, waited, issued); return; }
   waited = zc0 - 2;
-  if (!ring_wait(ring, zc0 - 1)) { ring_abort(ring, a, waited, issued); return; }
-  waited = zc0 - 1;
-  step_a(zc0 - 1);
+  if (!FIRST && a.dims == 3) {
+    const float4 pz = reinterpret_cast<Box4>(ring.slot(zc0 - 2, 3))[by][lane];
+    p0_t[2][0] = lo2(pz);
+    p0_t[2][1] = hi2(pz);
+  }
   __syncthreads();
 
-  for (int t = zc0 - 1; t <= zc1; ++t) {
-    // stage of plane t-1 is free from tick t on: refill it with plane t+3
-    if (t + 3 <= qlast) {
+  for (int t = zc0 - 2; t <= zc1; ++t) {
+    // plane t was last read in tick t-1, before that tick's barrier: refill
+    // its stage with plane t+NS
+    if (t + kTv2Stages <= qlast) {
       if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        ring_issue<FIRST>(ring, a, t + 3, i0, j0);
+        ring_issue<FIRST>(ring, a, t + kTv2Stages, i0, j0);
       }
-      issued = t + 3;
+      issued = t + kTv2Stages;
     }
-    if (!ring_wait(ring, t + 1)) { ring_abort(ring, a, waited, issued); return; }
-    waited = t + 1;
-    step_a(t + 1);
-    __syncthreads();
-    step_b(t);
-    __syncthreads();
+    // (a) u^0(t+1) from the box of plane t+1 (the wait is voted on below)
+    const int q = t + 1;
+    const bool ok = mbar_wait(ring.bar(q), ring.parity(q));
+    float2 v_n[2], p0_n[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}}, u0_n[2];
+    {
+      const float4 vv = reinterpret_cast<Box4>(ring.slot(q, 0))[by][lane];
+      v_n[0] = lo2(vv);
+      v_n[1] = hi2(vv);
+      u0_n[0] = v_n[0];
+      u0_n[1] = v_n[1];
+      if (!FIRST) {
+        float2(*px)[kTv2BoxW] = ring.slot(q, 1);
+        float2(*py)[kTv2BoxW] = ring.slot(q, 2);
+        const float4 px4 = reinterpret_cast<Box4>(px)[by][lane];
+        const float4 py4 = reinterpret_cast<Box4>(py)[by][lane];
+        const float4 pym4 = reinterpret_cast<Box4>(py)[by - 1][lane];
+        const float2 pxm0 = px[by][cm];
+        p0_n[0][0] = lo2(px4);
+        p0_n[0][1] = hi2(px4);
+        p0_n[1][0] = lo2(py4);
+        p0_n[1][1] = hi2(py4);
+        float2 mzlo = zero, mzhi = zero;
+        if (a.dims == 3) {
+          const float4 pz4 = reinterpret_cast<Box4>(ring.slot(q, 3))[by][lane];
+          p0_n[2][0] = lo2(pz4);
+          p0_n[2][1] = hi2(pz4);
+          mzlo = splat(q >= 1 ? 1.f : 0.f);
+          mzhi = splat(q <= a.nz - 2 ? -1.f : 0.f);
+        }
+        const float2 pxm[2] = {pxm0, p0_n[0][0]};
+        const float2 pym[2] = {lo2(pym4), hi2(pym4)};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float2 dh = e == 0 ? x2mul(mxlo0, pxm[0]) : pxm[1];
+          dh = e == 0 ? x2sub(dh, p0_n[0][0]) : x2fma(mxhi1, p0_n[0][1], dh);
+          dh = x2fma(mylo, pym[e], dh);
+          dh = x2fma(myhi, p0_n[1][e], dh);
+          if (a.dims == 3) {
+            dh = x2fma(mzlo, p0_t[2][e], dh);
+            dh = x2fma(mzhi, p0_n[2][e], dh);
+          }
+          u0_n[e] = x2fma(nmu, dh, v_n[e]);
+        }
+      }
+      XU0[q & 1][w][lane] = pack4(u0_n[0], u0_n[1]);
+    }
+    // (b) p^1(t)
+    if (t >= zc0 - 1) {
+      const float2 ux[2] = {u0_t[1], lo2(XU0[t & 1][w][ln])};
+      const float4 uy4 = XU0[t & 1][wn][lane];
+      const float2 uy[2] = {lo2(uy4), hi2(uy4)};
+      const float2 szhi = splat(a.dims == 3 && t <= a.nz - 2 ? a.step : 0.f);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        p1_t[0][e] = x2fma(e == 0 ? stp : sxhi1, x2sub(ux[e], u0_t[e]), p0_t[0][e]);
+        p1_t[1][e] = x2fma(syhi, x2sub(uy[e], u0_t[e]), p0_t[1][e]);
+        p1_t[2][e] = x2fma(szhi, x2sub(u0_n[e], u0_t[e]), p0_t[2][e]);
+        project2(p1_t[0][e], p1_t[1][e], p1_t[2][e]);
+      }
+      XP1[t & 1][w][lane] = pack4(p1_t[1][0], p1_t[1][1]);
+    }
+    if (!__syncthreads_and(ok)) { ring_abort(ring, a, waited, issued); return; }
+    waited = q;
+    // (c) u^1(t)
     if (t >= zc0) {
-      step_c(t);
-      __syncthreads();
-      if (t >= zc0 + 1) step_d(t - 1);
-      __syncthreads();
+      const float2 pxm[2] = {shfl_up2(p1_t[0][1]), p1_t[0][0]};
+      const float4 pym4 = XP1[t & 1][wp][lane];
+      const float2 pym[2] = {lo2(pym4), hi2(pym4)};
+      const float2 mzlo = splat(a.dims == 3 && t >= 1 ? 1.f : 0.f);
+      const float2 mzhi = splat(a.dims == 3 && t <= a.nz - 2 ? -1.f : 0.f);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float2 dh = e == 0 ? x2mul(mxlo0, pxm[0]) : pxm[1];
+        dh = e == 0 ? x2sub(dh, p1_t[0][0]) : x2fma(mxhi1, p1_t[0][1], dh);
+        dh = x2fma(mylo, pym[e], dh);
+        dh = x2fma(myhi, p1_t[1][e], dh);
+        if (a.dims == 3) {
+          dh = x2fma(mzlo, p1_prev[2][e], dh);
+          dh = x2fma(mzhi, p1_t[2][e], dh);
+        }
+        u1_t[e] = x2fma(nmu, dh, v_t[e]);
+      }
+      XU1[t & 1][w][lane] = pack4(u1_t[0], u1_t[1]);
+      // (d) p^2(t-1)
+      if (t >= zc0 + 1) {
+        const float2 ux[2] = {u1_prev[1], lo2(XU1[(t - 1) & 1][w][ln])};
+        const float4 uy4 = XU1[(t - 1) & 1][wn][lane];
+        const float2 uy[2] = {lo2(uy4), hi2(uy4)};
+        const float2 szhi = splat(a.dims == 3 && t - 1 <= a.nz - 2 ? a.step : 0.f);
+        float2 qo[3][2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          qo[0][e] = x2fma(e == 0 ? stp : sxhi1, x2sub(ux[e], u1_prev[e]), p1_prev[0][e]);
+          qo[1][e] = x2fma(syhi, x2sub(uy[e], u1_prev[e]), p1_prev[1][e]);
+          qo[2][e] = x2fma(szhi, x2sub(u1_t[e], u1_prev[e]), p1_prev[2][e]);
+          project2(qo[0][e], qo[1][e], qo[2][e]);
+        }
+        if (out_pair) {
+          const size_t gidx = (static_cast<size_t>(t - 1) * a.ny + gy) * a.nx + gx0;
+          *reinterpret_cast<float4*>(a.pout[0] + gidx) = pack4(qo[0][0], qo[0][1]);
+          *reinterpret_cast<float4*>(a.pout[1] + gidx) = pack4(qo[1][0], qo[1][1]);
+          if (a.dims == 3) *reinterpret_cast<float4*>(a.pout[2] + gidx) = pack4(qo[2][0], qo[2][1]);
+        }
+      }
+    }
+    // rotate the per-position state to the next plane
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      u0_t[e] = u0_n[e];
+      v_t[e] = v_n[e];
+      u1_prev[e] = u1_t[e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        p0_t[c][e] = p0_n[c][e];
+        p1_prev[c][e] = p1_t[c][e];
+      }
     }
   }
 }
@@ -622,21 +750,45 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms) {
+  if (nsteps != 2) return 32;
+  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks. Pick the
+  // chunk that minimises (waves, rounded up) x (ticks per chunk).
+  const long tiles = static_cast<long>((nx + TX2 - 1) / TX2) * ((ny + kTv2Ty - 1) / kTv2Ty);
+  int best = 32;
+  long best_cost = -1;
+  for (int zc : {16, 32, 64, 128, 256}) {
+    const int c = zc < nz ? zc : nz;
+    const long ctas = tiles * ((nz + c - 1) / c);
+    const long cost = ((ctas + sms - 1) / sms) * (c + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+    if (c == nz) break;
+  }
+  return best;
+}
+
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s) {
-  dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
+  if (nsteps == 2 && (a.nx & 1)) return cudaErrorInvalidValue;   // pairs of x positions
+  const int tx = nsteps == 2 ? TX2 : TX;
+  const int ty = nsteps == 2 ? kTv2Ty : TY;
+  dim3 grid((a.nx + tx - 1) / tx, (a.ny + ty - 1) / ty, (a.nz + a.zchunk - 1) / a.zchunk);
   auto kern = nsteps == 2 ? (first ? k_tv_step2<true> : k_tv_step2<false>)
                           : (first ? k_tv_step<true> : k_tv_step<false>);
   const int bytes = nsteps == 2 ? TvLayout2::kBytes : TvLayout1::kBytes;
+  const int threads = nsteps == 2 ? kTv2Threads : kTvThreads;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kTvThreads, bytes, s>>>(a);
+  kern<<<grid, threads, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 // 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box
-// of box_rows rows x 2 kTvBoxW floats x 1 plane, zero fill out of bounds.
+// of box_rows rows x 2 box_cols floats x 1 plane, zero fill out of bounds.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
-                             int box_rows) {
+                             int box_rows, int box_cols) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -654,7 +806,7 @@ cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, 
                               static_cast<cuuint64_t>(nz)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(8) * nx,
                                  static_cast<cuuint64_t>(8) * nx * ny};
-  const cuuint32_t box[3] = {2 * kTvBoxW, static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(2 * box_cols), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

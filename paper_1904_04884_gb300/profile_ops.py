@@ -23,6 +23,8 @@ def main():
     p.add_argument("--inner", type=int, default=20)
     p.add_argument("--iters", type=int, default=10)
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--tv-per-launch", type=int, default=1, choices=[1, 2],
+                   help="dual TV steps per kernel launch")
     a = p.parse_args()
 
     import torch
@@ -31,6 +33,7 @@ def main():
 
     dev = torch.device("cuda:0")
     h = Rihv(a.nx, a.ny, a.nz, 532e-9, 5e-6, 5e-3, 50e-6)
+    h.set_options(tv_steps_per_launch=a.tv_per_launch)
     shape = (a.nz, a.ny, a.nx)
     g = synth.Stream(1).normal(2 * a.nx * a.ny * a.nz).astype(np.float32).view(np.complex64)
     vol = torch.from_numpy(g.reshape(shape)).to(dev)
@@ -55,7 +58,7 @@ def main():
         elif a.op == "prox":
             h.prox_fused_lasso(vol, 0.01, 0.005, a.inner, out)
         else:
-            h.set_options(n_inner=a.inner, check_every=0)
+            h.set_options(n_inner=a.inner, check_every=0, tv_steps_per_launch=a.tv_per_launch)
             h.solve(holo, 0.01, 0.005, a.iters, out)
 
     once()

@@ -96,7 +96,7 @@ def test_adjoint_identity_on_gpu():
 @pytest.mark.parametrize("per_launch", [1, 2])
 @pytest.mark.parametrize("dims", [3, 2])
 @pytest.mark.parametrize("nx,ny,nz,k", [(48, 24, 37, 20), (24, 16, 5, 1), (64, 32, 33, 7),
-                                         (16, 16, 1, 5)])
+                                         (16, 16, 1, 5), (96, 48, 70, 6)])
 def test_prox_parity(nx, ny, nz, k, dims, per_launch):
     op = optics(nx, ny, nz)
     v = synth.random_complex(synth.Stream(nz * 3 + k), op.shape)
