@@ -282,6 +282,7 @@ def test_full_size_prox(mid):
     v = synth.random_complex(synth.Stream(103), op.shape).astype(np.complex64)
     out = torch.empty(op.shape, dtype=torch.complex64, device=dev())
     h.set_options(tv_dims=3)
-    h.prox_fused_lasso(to_dev(v), 0.2, 0.05, 2, out)
-    ref = O.prox_fused_lasso(v.astype(np.complex128), 0.2, 0.05, 2, 3)
+    # 4 dual steps: the first two-step launch (p = 0) and one reading p
+    h.prox_fused_lasso(to_dev(v), 0.2, 0.05, 4, out)
+    ref = O.prox_fused_lasso(v.astype(np.complex128), 0.2, 0.05, 4, 3)
     assert rel_l2(out.cpu().numpy(), ref) <= OP_TOL
