@@ -377,6 +377,228 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident engine for power-of-two lengths N (64 ... 1024).
+//
+// One transform is held by a team of N/8 threads, thread i owning the eight
+// elements x[i + (N/8) e], e = 0..7. Every Stockham pass (radix 8, the last
+// one 2 or 4 when N is not a power of 8) reads exactly that set: butterfly
+// b = i + (N/8) q of radix R takes x[b + j N/R], i.e. element e = q + j (8/R)
+// of the thread. Its outputs go to (b - k) R + k + m p (k = b mod p, p the
+// product of the earlier radices); for the last pass that is b + m N/R, the
+// same per-thread set again, so the result stays in registers in natural
+// order. Passes in between exchange through shared memory (one barrier per
+// exchange, two buffers alternating), indexed l ^ ((l >> 3) & 15), which
+// makes every half-warp's 8-byte accesses of all passes conflict-free with
+// four interleaved teams (thread = 4 i + team, rows 4 elements apart). The
+// first pass reads from global memory and the last writes to it directly.
+// ---------------------------------------------------------------------------
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+template <int N>
+struct RShape {
+  static constexpr int TT = N / 8;                                  // threads per transform
+  static constexpr int NP = ilog2c(N) / 3 + (ilog2c(N) % 3 ? 1 : 0);  // passes
+  static constexpr int LDX = N + 4;                                 // exchange row stride
+  static constexpr int kTeams = 4;                                  // transforms per CTA
+  static constexpr int kThreads = kTeams * TT;
+  __host__ __device__ static constexpr int radix(int s) {
+    return s < ilog2c(N) / 3 ? 8 : (1 << (ilog2c(N) % 3));
+  }
+  static constexpr size_t smem_bytes() {
+    return sizeof(float2) * (static_cast<size_t>(N) + 2 * kTeams * static_cast<size_t>(LDX));
+  }
+};
+
+__device__ __forceinline__ int xswz(int l) { return l ^ ((l >> 3) & 15); }
+
+template <int N, bool INV, int S, int P>
+__device__ __forceinline__ void rfft_passes(float2 (&v)[8], int i, float2* xa, float2* xb,
+                                            const float2* __restrict__ tw) {
+  if constexpr (S < RShape<N>::NP) {
+    constexpr int R = RShape<N>::radix(S);
+    constexpr int TT = RShape<N>::TT;
+    constexpr bool LAST = S == RShape<N>::NP - 1;
+    float2* xs = (S & 1) ? xb : xa;
+#pragma unroll
+    for (int q = 0; q < 8 / R; ++q) {
+      const int b = i + q * TT;
+      const int k = b & (P - 1);
+      float2 u[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) u[j] = v[q + j * (8 / R)];
+      if constexpr (P > 1) {
+#pragma unroll
+        for (int j = 1; j < R; ++j) {
+          const float2 w = tw[j * k * (N / (P * R))];
+          u[j] = INV ? cmulc(u[j], w) : cmul(u[j], w);
+        }
+      }
+      Dft<R, INV>::run(u);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if constexpr (LAST)
+          v[q + m * (8 / R)] = u[m];
+        else
+          xs[xswz((b - k) * R + k + m * P)] = u[m];
+      }
+    }
+    if constexpr (!LAST) {
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = xs[xswz(i + TT * e)];
+    }
+    rfft_passes<N, INV, S + 1, P * R>(v, i, xa, xb, tw);
+  }
+}
+
+// One transform per team; afterwards the caller's buffers are swapped when
+// the number of exchanges is odd, so consecutive transforms keep alternating.
+template <int N, bool INV>
+__device__ __forceinline__ void rfft(float2 (&v)[8], int i, float2*& xa, float2*& xb,
+                                     const float2* __restrict__ tw) {
+  rfft_passes<N, INV, 0, 1>(v, i, xa, xb, tw);
+  if constexpr ((RShape<N>::NP - 1) % 2 == 1) {
+    float2* t = xa;
+    xa = xb;
+    xb = t;
+  }
+}
+
+// Row pass, register engine: four rows of one plane per item (team = row).
+template <bool INV, int IN, int OUT, int EPI, int N>
+__global__ void __launch_bounds__(RShape<N>::kThreads) k_rows_reg(const __grid_constant__ RowArgs a) {
+  using Sh = RShape<N>;
+  constexpr int TT = Sh::TT, W = kStrip, NT = Sh::kTeams;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = a.tw[m];
+  const int i = threadIdx.x / NT, team = threadIdx.x % NT;
+  float2* xa = smem + N + team * Sh::LDX;
+  float2* xb = xa + NT * Sh::LDX;
+  constexpr int nstrip = N / W;
+  const int rblocks = a.ny / NT;
+  const int nitems = rblocks * a.nz;
+  __syncthreads();
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int row = (item % rblocks) * NT + team;
+    const size_t z = item / rblocks;
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = i + TT * e;
+      if (IN == ROW_IN_STRIP) {
+        v[e] = static_cast<const float2*>(a.src)[((z * nstrip + c / W) * a.ny + row) * W + (c % W)];
+      } else {
+        const size_t gi = (z * a.ny + row) * N + c;
+        if (IN == ROW_IN_F32)
+          v[e] = make_float2(static_cast<const float*>(a.src)[gi], 0.f);
+        else
+          v[e] = static_cast<const float2*>(a.src)[gi];
+      }
+    }
+    rfft<N, INV>(v, i, xa, xb, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = i + TT * e;
+      if (OUT == ROW_OUT_STRIP) {
+        a.dst[((z * nstrip + c / W) * a.ny + row) * W + (c % W)] = cscale(v[e], a.scale);
+      } else {
+        const size_t gi = (z * a.ny + row) * N + c;
+        if (EPI == ROW_EPI_GRAD) {
+          const float2 y = a.y[gi];
+          a.dst[gi] = make_float2(y.x - a.scale * v[e].x, y.y - a.scale * v[e].y);
+        } else {
+          a.dst[gi] = cscale(v[e], a.scale);
+        }
+      }
+    }
+  }
+}
+
+// Column pass, register engine: one strip of kStrip columns (team = column),
+// transforms of length N = ny along y; element (y, w) of the strip at y*kStrip + w.
+template <int MODE, int N>
+__global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_constant__ ColArgs a) {
+  using Sh = RShape<N>;
+  constexpr int TT = Sh::TT, W = kStrip, NT = Sh::kTeams;
+  static_assert(NT == W, "one team per strip column");
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = a.tw[m];
+  const int i = threadIdx.x / NT, w = threadIdx.x % NT;
+  float2* xa = smem + N + w * Sh::LDX;
+  float2* xb = xa + NT * Sh::LDX;
+  const int s = blockIdx.x;
+  const int nstrip = a.nx / W;
+  constexpr size_t strip_elems = static_cast<size_t>(N) * W;
+  __syncthreads();
+
+  if (MODE == COL_FWD_ZSUM || MODE == COL_ADJ_GEN) {
+    const int z0 = blockIdx.y * a.z_per_group;
+    const int z1 = min(a.nz, z0 + a.z_per_group);
+    // transfer-function phases and band mask of this thread's frequencies
+    uint2 ph[8];
+    float amp[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t o = s * strip_elems + (i + TT * e) * W + w;
+      ph[e] = __ldg(a.phase + o);
+      amp[e] = __ldg(a.amp + o);
+    }
+    if (MODE == COL_FWD_ZSUM) {
+      float2 acc[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = make_float2(0.f, 0.f);
+      for (int z = z0; z < z1; ++z) {
+        const float2* src = a.src + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
+        float2 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = src[(i + TT * e) * W + w];
+        rfft<N, false>(v, i, xa, xb, tw);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+      }
+      float2* dst = a.dst + static_cast<size_t>(blockIdx.y) * a.nx * a.ny;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        dst[static_cast<size_t>(i + TT * e) * a.nx + s * W + w] = acc[e];
+    } else {
+      float2 rr[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        rr[e] = cscale(a.src[static_cast<size_t>(i + TT * e) * a.nx + s * W + w], a.scale);
+      for (int z = z0; z < z1; ++z) {
+        float2 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = cmulc(rr[e], transfer(ph[e], amp[e], z));
+        rfft<N, true>(v, i, xa, xb, tw);
+        float2* dst = a.dst + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[(i + TT * e) * W + w] = v[e];
+      }
+    }
+  } else if (MODE == COL_PLAIN_FWD) {
+    // strip-major plane 0 -> row-major spectrum
+    const float2* src = a.src + static_cast<size_t>(s) * strip_elems;
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = src[(i + TT * e) * W + w];
+    rfft<N, false>(v, i, xa, xb, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      a.dst[static_cast<size_t>(i + TT * e) * a.nx + s * W + w] = cscale(v[e], a.scale);
+  } else {  // COL_PLAIN_INV: row-major spectrum -> strip-major plane 0
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = a.src[static_cast<size_t>(i + TT * e) * a.nx + s * W + w];
+    rfft<N, true>(v, i, xa, xb, tw);
+    float2* dst = a.dst + static_cast<size_t>(s) * strip_elems;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) dst[(i + TT * e) * W + w] = cscale(v[e], a.scale);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // z-group reduction of the forward spectrum, residual and ||r||^2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double block_sum(double v) {
@@ -430,8 +652,50 @@ __global__ void __launch_bounds__(kRedThreads) k_zsum(const float2* partial, int
   }
 }
 
+template <bool INV, int IN, int OUT, int EPI, int N>
+cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
+  using Sh = RShape<N>;
+  auto kern = k_rows_reg<INV, IN, OUT, EPI, N>;
+  const int smem = static_cast<int>(Sh::smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int sms = 152, dev = 0, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int items = (a.ny / Sh::kTeams) * a.nz;
+  const int grid = items < per_sm * sms ? items : per_sm * sms;
+  kern<<<grid, Sh::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int N>
+cudaError_t launch_cols_reg(const ColArgs& a, int groups, cudaStream_t s) {
+  using Sh = RShape<N>;
+  auto kern = k_cols_reg<MODE, N>;
+  const int smem = static_cast<int>(Sh::smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.nx / kStrip, groups);
+  kern<<<grid, Sh::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Lengths served by the register engine.
+bool reg_length(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
+
 template <bool INV, int IN, int OUT, int EPI>
 cudaError_t launch_rows_t(const RowArgs& a, cudaStream_t s) {
+  switch (a.nx) {
+    case 64: return launch_rows_reg<INV, IN, OUT, EPI, 64>(a, s);
+    case 128: return launch_rows_reg<INV, IN, OUT, EPI, 128>(a, s);
+    case 256: return launch_rows_reg<INV, IN, OUT, EPI, 256>(a, s);
+    case 512: return launch_rows_reg<INV, IN, OUT, EPI, 512>(a, s);
+    case 1024: return launch_rows_reg<INV, IN, OUT, EPI, 1024>(a, s);
+    default: break;
+  }
   const size_t smem = rows_smem_bytes(a.nx);
   auto kern = k_rows<INV, IN, OUT, EPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -448,6 +712,14 @@ cudaError_t launch_rows_t(const RowArgs& a, cudaStream_t s) {
 
 template <int MODE>
 cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
+  switch (a.ny) {
+    case 64: return launch_cols_reg<MODE, 64>(a, groups, s);
+    case 128: return launch_cols_reg<MODE, 128>(a, groups, s);
+    case 256: return launch_cols_reg<MODE, 256>(a, groups, s);
+    case 512: return launch_cols_reg<MODE, 512>(a, groups, s);
+    case 1024: return launch_cols_reg<MODE, 1024>(a, groups, s);
+    default: break;
+  }
   const size_t smem = cols_smem_bytes(MODE, a.ny);
   auto kern = k_cols<MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -461,12 +733,28 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 }  // namespace
 
 size_t rows_smem_bytes(int nx) {
+  if (reg_length(nx)) return sizeof(float2) * (nx + 2 * 4 * static_cast<size_t>(nx + 4));
   return sizeof(float2) * (2 * static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
 }
 
 size_t cols_smem_bytes(int mode, int ny) {
   (void)mode;
+  if (reg_length(ny)) return sizeof(float2) * (ny + 2 * 4 * static_cast<size_t>(ny + 4));
   return sizeof(float2) * (2 * static_cast<size_t>(ny) * (kStrip + 1) + ny);
+}
+
+int cols_ctas_per_sm(int ny) {
+  int per_sm = 2;
+  cudaError_t e = cudaSuccess;
+  switch (ny) {
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols_reg<COL_FWD_ZSUM, 64>, RShape<64>::kThreads, RShape<64>::smem_bytes()); break;
+    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols_reg<COL_FWD_ZSUM, 128>, RShape<128>::kThreads, RShape<128>::smem_bytes()); break;
+    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols_reg<COL_FWD_ZSUM, 256>, RShape<256>::kThreads, RShape<256>::smem_bytes()); break;
+    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols_reg<COL_FWD_ZSUM, 512>, RShape<512>::kThreads, RShape<512>::smem_bytes()); break;
+    case 1024: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cols_reg<COL_FWD_ZSUM, 1024>, RShape<1024>::kThreads, RShape<1024>::smem_bytes()); break;
+    default: break;
+  }
+  return (e == cudaSuccess && per_sm >= 1) ? per_sm : 1;
 }
 
 cudaError_t launch_rows(int inv, int in, int out, int epi, const RowArgs& a, cudaStream_t s) {

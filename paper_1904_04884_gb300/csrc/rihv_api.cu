@@ -353,7 +353,7 @@ constexpr int kMaxGroups = 32;
 
 void choose_groups(rihv_ctx* h, int nz) {
   const int strips = h->nx / kStrip;
-  const double slots = 2.0 * h->sms;
+  const double slots = static_cast<double>(cols_ctas_per_sm(h->ny)) * h->sms;
   int best_zpg = nz;
   double best_eff = -1.0;
   for (int zpg = nz; zpg >= 1; --zpg) {

@@ -104,6 +104,8 @@ cudaError_t launch_rows(int dir_inverse, int in, int out, int epi, const RowArgs
 cudaError_t launch_cols(int mode, const ColArgs& a, int groups, cudaStream_t s);
 size_t rows_smem_bytes(int nx);
 size_t cols_smem_bytes(int mode, int ny);
+// Resident CTAs per SM of the forward column pass for this ny (sizes the z-groups).
+int cols_ctas_per_sm(int ny);
 
 // S = sum_g partial[g]; if bhat: out = S - bhat and ||out||^2 / (nx ny) -> sc->rnorm2.
 cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, float2* out,

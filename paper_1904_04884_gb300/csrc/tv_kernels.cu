@@ -43,13 +43,9 @@ constexpr int slot_bytes(int bw, int bh) { return ((bw * bh * 8 + 127) / 128) * 
 constexpr int SLOT1 = slot_bytes(BW, BH1);
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls before giving up
 
-// Regions (x extent, y extent) relative to the tile origin (i0, j0):
-//   A  = u of the first step:   x in [-1, TX+1], y in [-1, TY+1]
-//   R2 = p of the first step:   x in [-1, TX],   y in [-1, TY]
-//   R1 = u of the last step:    x in [0, TX],    y in [0, TY]
-//   T  = output tile:           x in [0, TX),    y in [0, TY)
-constexpr int AX = TX + 3, AY = TY + 3;
-constexpr int R2X = TX + 2, R2Y = TY + 2;
+// One-step kernel: u = v - mu D^H p is formed on the tile plus one column and
+// one row (x in [0, TX], y in [0, TY] relative to the tile origin), the region
+// whose forward differences the tile's p update reads.
 constexpr int R1X = TX + 1, R1Y = TY + 1;
 
 // ---- PTX helpers (TMA + mbarrier) -----------------------------------------
@@ -110,7 +106,6 @@ struct PlaneRing {
   static constexpr int kW = BWR;
   static constexpr int kH = BH;
   static constexpr int kY0 = Y0;   // box row of the tile's first row
-  static constexpr int kStages = NS;
   unsigned char* smem;
   unsigned long long* bars;
   int base;                        // first plane of the ring (q - base >= 0)
@@ -285,7 +280,7 @@ struct TvLayout2 {   // two dual steps per launch
 };
 
 // Packed two-lane FP32 arithmetic (f32x2, sm_100 and later) on complex
-// values: one instruction per complex add, subtract, multiply-add or scale,
+// values: one instruction per complex subtract, multiply-add or scale,
 // each lane rounded as the scalar instruction would.
 __device__ __forceinline__ unsigned long long as_b64(float2 a) {
   unsigned long long r;
@@ -296,11 +291,6 @@ __device__ __forceinline__ float2 as_f2(unsigned long long r) {
   float2 a;
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
   return a;
-}
-__device__ __forceinline__ float2 x2add(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_b64(a)), "l"(as_b64(b)));
-  return as_f2(d);
 }
 __device__ __forceinline__ float2 x2sub(float2 a, float2 b) {
   unsigned long long d;
