@@ -510,6 +510,13 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_rows_reg(const __grid_c
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = nxt[e];
     if (item + gridDim.x < nitems) load(item + gridDim.x, nxt);
+    // the gradient step's y is loaded before the transform, so that its
+    // latency overlaps the transform and no store waits on a load
+    float2 yv[8];
+    if (OUT != ROW_OUT_STRIP && EPI == ROW_EPI_GRAD) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) yv[e] = a.y[(z * a.ny + row) * N + i + TT * e];
+    }
     rfft<N, INV>(v, i, xa, xb, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -519,8 +526,7 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_rows_reg(const __grid_c
       } else {
         const size_t gi = (z * a.ny + row) * N + c;
         if (EPI == ROW_EPI_GRAD) {
-          const float2 y = a.y[gi];
-          a.dst[gi] = make_float2(y.x - a.scale * v[e].x, y.y - a.scale * v[e].y);
+          a.dst[gi] = make_float2(yv[e].x - a.scale * v[e].x, yv[e].y - a.scale * v[e].y);
         } else {
           a.dst[gi] = cscale(v[e], a.scale);
         }
@@ -563,11 +569,21 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
       float2 acc[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] = make_float2(0.f, 0.f);
+      float2 nxt[8];   // the next plane's loads are issued before this plane's transform
+      if (z0 < z1) {
+        const float2* src = a.src + (static_cast<size_t>(z0) * nstrip + s) * strip_elems;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
+      }
       for (int z = z0; z < z1; ++z) {
-        const float2* src = a.src + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
         float2 v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = src[(i + TT * e) * W + w];
+        for (int e = 0; e < 8; ++e) v[e] = nxt[e];
+        if (z + 1 < z1) {
+          const float2* src = a.src + (static_cast<size_t>(z + 1) * nstrip + s) * strip_elems;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
+        }
         rfft<N, false>(v, i, xa, xb, tw);
 #pragma unroll
         for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
