@@ -353,9 +353,14 @@ def main():
     tv_ms, tv_launches = stages["tv"]
     # 32 B/voxel for the launch that starts from p = 0 (reads v, writes p),
     # 56 B/voxel for every other launch (reads v and p, writes p), whatever
-    # number of dual steps a launch performs.
+    # number of dual steps a launch performs; the last launch with the fused
+    # finalize reads v and p and x_{k-1}, y_k and writes x_k, y_{k+1} instead
+    # of p: 64 B/voxel.
     per_prox = tv_launches // (args.steps * (w.iters + 0)) if tv_launches else 1
-    alg_bytes_per_launch = w.nvox * (32 + 56 * (per_prox - 1)) / max(per_prox, 1)
+    fused = (h.options.tv_steps_per_launch == 2 and h.options.fuse_finalize == 1
+             and w.n_inner % 2 == 0 and per_prox >= 2)
+    alg = 32 + 56 * (per_prox - 1) + (64 - 56 if fused else 0)
+    alg_bytes_per_launch = w.nvox * alg / max(per_prox, 1)
     avg_launch_s = (tv_ms / 1e3) / max(tv_launches, 1)
     achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if tv_launches else None
     peak, peak_kind = hbm_peak()
@@ -392,6 +397,7 @@ def main():
                      "traffic": measured_traffic(w.nvox, tv_kernel), "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes_per_launch,
                      "dual_steps_per_launch": h.options.tv_steps_per_launch,
+                     "fused_finalize": bool(fused),
                      "avg_launch_ms": avg_launch_s * 1e3},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "time_to_tolerance": ttt,

@@ -57,7 +57,7 @@ typedef enum {
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
- * tv_steps_per_launch 2. */
+ * tv_steps_per_launch 2, fuse_finalize 1. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -72,6 +72,11 @@ typedef struct {
                         recomputed on a one-voxel halo ring; an odd step
                         count ends with a one-step launch). 2 needs nx even,
                         which every supported size is.                       */
+  int fuse_finalize; /* 1: with two steps per launch and an even step count,
+                        the last TV launch also forms x = soft(v - mu D^H p)
+                        (and FISTA's y and restart product), so the final
+                        dual never reaches memory; 0: separate finalize
+                        kernel. Same arithmetic either way.                  */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */

@@ -72,6 +72,8 @@ struct rihv_ctx {
   int groups = 1, zpg = 1;
   int sms = 152;
   int tv_zchunk = 0;                 // planes per TV z-chunk; 0: tv_default_zchunk
+  double* fin_partials = nullptr;    // one per CTA of a fused-finalize TV launch
+  int fin_ctas = 0;                  // capacity of fin_partials
   double tau = 0;
   FftPlan plan_x{}, plan_y{};
   std::string err;
@@ -97,7 +99,7 @@ struct rihv_ctx {
   int trace_cap = 0;
   int* det_err = nullptr;
   int* tv_err = nullptr;       // set by a TV kernel whose bounded wait gave up
-  CUtensorMap tm_pa[2][3], tm_pb[2][3];   // [one-step box, two-step box]
+  CUtensorMap tm_pa[3][3], tm_pb[3][3];   // [one-step, two-step, fused-finalize box]
   DetectWork det{};
   std::vector<void*> allocs;
 
@@ -282,16 +284,21 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
   return RIHV_OK;
 }
 
-// K dual steps; returns the buffer set holding the final p.
-rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
+// K dual steps; returns the buffer set holding the final p. With `fin` (two
+// steps per launch, K even) the last launch also runs the finalize and
+// *pfinal is null.
+rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal,
+                     const FinArgs* fin = nullptr, int fin_mode = FIN_PROX) {
   // With tv_steps_per_launch = 2, two dual steps per launch and a single-step
   // launch for an odd remainder.
   const int per = h->opt.tv_steps_per_launch;
   const int launches = per == 2 ? k / 2 + (k % 2) : k;
+  const bool fused = fin && per == 2 && k >= 2 && k % 2 == 0;
   StageScope sc(h, ST_TV, launches);
-  CUtensorMap tm_v[2];
+  CUtensorMap tm_v[3];
   CK(make_volume_tmap(&tm_v[0], v, h->nx, h->ny, h->nz, kTvBoxH1, kTvBoxW));
   if (per == 2) CK(make_volume_tmap(&tm_v[1], v, h->nx, h->ny, h->nz, kTv2BoxH, kTv2BoxW));
+  if (fused) CK(make_volume_tmap(&tm_v[2], v, h->nx, h->ny, h->nz, kTv2BoxHF, kTv2BoxW));
   TvArgs a{};
   a.err = h->tv_err;
   a.nx = h->nx;
@@ -299,27 +306,44 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   a.nz = h->nz;
   a.dims = h->opt.tv_dims;
   const int zc_auto = tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
+  const int zc_final = tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true);
   a.mu = mu;
   a.step = 1.f / (4.f * a.dims * mu);
+  if (fused) {
+    a.fin_mode = fin_mode;
+    a.kappa = fin->kappa;
+    a.x_prev = fin->x_prev;
+    a.y = fin->y;
+    a.x_out = fin->x_out;
+    a.y_out = fin->y_out;
+    a.sc = fin->sc;
+    a.fin_partials = h->fin_partials;
+    a.fin_ticket = h->red.tickets + 3;
+  }
   float2** src = h->pb;
   float2** dst = h->pa;
   bool src_is_b = true;
   int done = 0;
   while (done < k) {
     const int n = (per == 2 && k - done >= 2) ? 2 : 1;
-    const int b = n == 2 ? 1 : 0;
-    a.zchunk = h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32);
+    const bool last = done + n == k;
+    const int b = n == 2 ? ((fused && last) ? 2 : 1) : 0;
+    // the fused-finalize launch has its own tile, so its own default chunk
+    a.zchunk = (fused && last) ? zc_final
+                               : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32));
+    if (fused && last && tv_final_ctas(h->nx, h->ny, h->nz, a.zchunk) > h->fin_ctas)
+      return fail(h, RIHV_ERR_INVALID_ARG, "z-chunk too small for the fused finalize");
     a.tm_v = tm_v[b];
     for (int c = 0; c < 3; ++c) {
       a.tm_p[c] = src_is_b ? h->tm_pb[b][c] : h->tm_pa[b][c];
       a.pout[c] = dst[c];
     }
-    CK(launch_tv_step(done == 0, n, a, h->stream));
+    CK(launch_tv_step(done == 0, n, a, h->stream, fused && last));
     done += n;
     std::swap(src, dst);
     src_is_b = !src_is_b;
   }
-  *pfinal = src;
+  *pfinal = fused ? nullptr : src;
   return RIHV_OK;
 }
 
@@ -327,11 +351,8 @@ rihv_status prox_into(rihv_ctx* h, const float2* v, float t_l1, float t_tv, int 
                       float2* x_out) {
   float2* const* pf = nullptr;
   const bool tv = (t_tv > 0.f && k > 0);
-  if (tv) CKS(tv_steps(h, v, t_tv, k, &pf));
-  StageScope sc(h, ST_FINAL, mode == FIN_FISTA ? 2 : 1);
   FinArgs f{};
   f.v = v;
-  for (int c = 0; c < 3; ++c) f.p[c] = tv ? pf[c] : nullptr;
   f.x_prev = h->x;
   f.y = h->y;
   f.x_out = x_out;
@@ -344,8 +365,16 @@ rihv_status prox_into(rihv_ctx* h, const float2* v, float t_l1, float t_tv, int 
   f.kappa = t_l1;
   f.sc = h->sc;
   f.w = h->red;
-  CK(launch_finalize(mode, f, h->stream));
-  if (mode == FIN_FISTA) CK(launch_restart_fixup(x_out, h->y, h->nvox, h->sc, h->stream));
+  if (tv) CKS(tv_steps(h, v, t_tv, k, &pf, h->opt.fuse_finalize ? &f : nullptr, mode));
+  if (!tv || pf) {
+    StageScope sc(h, ST_FINAL, mode == FIN_FISTA ? 2 : 1);
+    for (int c = 0; c < 3; ++c) f.p[c] = tv ? pf[c] : nullptr;
+    CK(launch_finalize(mode, f, h->stream));
+    if (mode == FIN_FISTA) CK(launch_restart_fixup(x_out, h->y, h->nvox, h->sc, h->stream));
+  } else if (mode == FIN_FISTA) {
+    StageScope sc(h, ST_FINAL, 1);
+    CK(launch_restart_fixup(x_out, h->y, h->nvox, h->sc, h->stream));
+  }
   return RIHV_OK;
 }
 
@@ -458,6 +487,7 @@ void rihv_default_options(rihv_options* o) {
   o->tol = 0.0;
   o->f_star = 0.0;
   o->tv_steps_per_launch = 2;
+  o->fuse_finalize = 1;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -518,6 +548,8 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   }
   AL(h->sc, 1);
   AL(h->red.partials, 4 * kRedBlocks);
+  h->fin_ctas = tv_final_ctas(nx, ny, nz, 8);   // the smallest z-chunk the tuner tries
+  AL(h->fin_partials, h->fin_ctas);
   AL(h->red.tickets, 8);
   AL(h->det_err, 1);
   AL(h->tv_err, 1);
@@ -526,9 +558,9 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
       cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(h->tv_err, 0, sizeof(int)) != cudaSuccess)
     return cleanup(fail(h, RIHV_ERR_CUDA, "memset failed"));
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 3; ++b)
     for (int c = 0; c < 3; ++c) {
-      const int rows = b == 0 ? kTvBoxH1 : kTv2BoxH;
+      const int rows = b == 0 ? kTvBoxH1 : (b == 1 ? kTv2BoxH : kTv2BoxHF);
       const int cols = b == 0 ? kTvBoxW : kTv2BoxW;
       if (make_volume_tmap(&h->tm_pa[b][c], h->pa[c], nx, ny, nz, rows, cols) != cudaSuccess ||
           make_volume_tmap(&h->tm_pb[b][c], h->pb[c], nx, ny, nz, rows, cols) != cudaSuccess)
@@ -611,7 +643,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
   if ((o->tv_dims != 2 && o->tv_dims != 3) || o->n_inner < 0 || o->check_every < 0 ||
       o->tol < 0 || o->f_star < 0 || (o->restart != 0 && o->restart != 1) ||
       (o->accelerate != 0 && o->accelerate != 1) ||
-      (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2))
+      (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2) ||
+      (o->fuse_finalize != 0 && o->fuse_finalize != 1))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   h->opt = *o;
   return RIHV_OK;
@@ -846,7 +879,7 @@ rihv_status rihv_batch_destroy(rihv_batch b) {
 static bool same_options(const rihv_options& a, const rihv_options& o) {
   return a.tv_dims == o.tv_dims && a.restart == o.restart && a.accelerate == o.accelerate &&
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
-         a.tv_steps_per_launch == o.tv_steps_per_launch;
+         a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize;
 }
 
 static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, bool warm) {

@@ -37,6 +37,13 @@ constexpr int kTv2Threads = 32 * kTv2Warps;
 constexpr int kTv2BoxW = kTv2Tx + 4;
 constexpr int kTv2BoxH = kTv2Ty + 4;
 constexpr int kTv2Stages = 3;
+// The launch with the fused finalize needs one more halo ring on the low
+// sides (D^H of the final dual): a 58 x 11 tile, box 64 x 16 from (i0-4,
+// j0-3), 15 warps (fewer threads leave room for its extra per-thread state).
+constexpr int kTv2TxF = 58;
+constexpr int kTv2TyF = 11;
+constexpr int kTv2WarpsF = kTv2TyF + 4;
+constexpr int kTv2BoxHF = kTv2WarpsF + 1;
 
 constexpr int kRedBlocks = 1216;   // fixed grid of the streaming reduction kernels (8 x 152)
 constexpr int kRedThreads = 256;
@@ -114,6 +121,7 @@ cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, f
 // ---------------------------------------------------------------------------
 // TV / prox / FISTA kernels (tv_kernels.cu)
 // ---------------------------------------------------------------------------
+struct DevScalars;
 struct TvArgs {
   CUtensorMap tm_v;    // v (see make_volume_tmap; box height per schedule)
   CUtensorMap tm_p[3]; // dual input p_x, p_y, p_z
@@ -123,11 +131,28 @@ struct TvArgs {
   int zchunk;
   float mu;            // t_tv
   float step;          // 1 / (4 dims mu)
+  // Fused finalize (the last two-step launch of a prox writes x = soft(v -
+  // mu D^H p, kappa) instead of p; in FISTA mode also y_{k+1} and the
+  // restart reduction, exactly as the finalize kernel).
+  int fin_mode;        // FinMode
+  float kappa;         // t_l1
+  const float2* x_prev;
+  const float2* y;
+  float2* x_out;
+  float2* y_out;
+  DevScalars* sc;
+  double* fin_partials;   // one double per CTA of the launch
+  unsigned* fin_ticket;   // last-block counter (reset by the last block)
 };
-// nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero.
-cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s);
-// Planes per z-chunk of the TV launch grid when none was tuned.
-int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms);
+// nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero;
+// final (two-step launches only): fused finalize, no dual output.
+cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s,
+                           bool final = false);
+// CTAs of a fused-finalize launch (sizes fin_partials).
+int tv_final_ctas(int nx, int ny, int nz, int zchunk);
+// Planes per z-chunk of the TV launch grid when none was tuned (final: the
+// fused-finalize launch's tile).
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false);
 // Box of box_rows x box_cols complex elements: (kTvBoxH1, kTvBoxW) for the
 // one-step kernel, (kTv2BoxH, kTv2BoxW) for the two-step kernel.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,

@@ -100,12 +100,13 @@ __device__ __forceinline__ void project(float2& qx, float2& qy, float2& qz) {
 // Plane ring fed by TMA: NS stages x 4 slots (v, p_x, p_y, p_z) of a
 // BH x BWR box each. Plane q lives in stage (q - base) mod NS; its n-th use
 // has mbarrier parity n&1.
-template <int BWR, int BH, int Y0, int NS>
+template <int BWR, int BH, int Y0, int NS, int X0 = 2>
 struct PlaneRing {
   static constexpr int kSlot = slot_bytes(BWR, BH);
   static constexpr int kW = BWR;
   static constexpr int kH = BH;
   static constexpr int kY0 = Y0;   // box row of the tile's first row
+  static constexpr int kX0 = X0;   // box column of the tile's first column
   unsigned char* smem;
   unsigned long long* bars;
   int base;                        // first plane of the ring (q - base >= 0)
@@ -124,7 +125,7 @@ __device__ __forceinline__ void ring_issue(const Ring& r, const TvArgs& a, int q
   const int nslots = FIRST ? 1 : (a.dims == 3 ? 4 : 3);
   const unsigned bar = r.bar(q);
   mbar_expect_tx(bar, static_cast<unsigned>(nslots * Ring::kW * Ring::kH * 8));
-  const int x = 2 * (i0 - 2), y = j0 - Ring::kY0;
+  const int x = 2 * (i0 - Ring::kX0), y = j0 - Ring::kY0;
   tma_load_3d(smem_addr(r.slot(q, 0)), &a.tm_v, x, y, q, bar);
   if (!FIRST) {
     tma_load_3d(smem_addr(r.slot(q, 1)), &a.tm_p[0], x, y, q, bar);
@@ -265,17 +266,96 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
   }
 }
 
-constexpr int TX2 = kTv2Tx;
-constexpr int NW2 = kTv2Warps;
-constexpr int SLOT2 = slot_bytes(kTv2BoxW, kTv2BoxH);
-using Ring2 = PlaneRing<kTv2BoxW, kTv2BoxH, 2, kTv2Stages>;
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < static_cast<int>(blockDim.x >> 5)) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
 
-struct TvLayout2 {   // two dual steps per launch
-  static constexpr int kXOff = kTv2Stages * 4 * SLOT2;
+// Writes this block's partial (slot `which`) and returns true in every thread
+// of the last block to arrive, which then owns the final sum.
+__device__ __forceinline__ bool publish_partial(double bs, RedWork w, int which, int ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    w.partials[which * kRedBlocks + blockIdx.x] = bs;
+    __threadfence();
+    last = atomicAdd(&w.tickets[ticket], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ __forceinline__ double final_sum(RedWork w, int which) {
+  __threadfence();
+  double v = 0.0;
+  for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
+    v += static_cast<volatile double*>(w.partials)[which * kRedBlocks + b];
+  return block_sum(v);
+}
+
+// The same shrinkage through the reciprocal square root (one hardware
+// approximation instead of a square root and a division; 2 ulp).
+__device__ __forceinline__ float2 soft_rsqrt(float2 u, float kappa) {
+  const float m2 = u.x * u.x + u.y * u.y;
+  const float s = (m2 > kappa * kappa) ? (1.f - kappa * rsqrtf(m2)) : 0.f;
+  return make_float2(u.x * s, u.y * s);
+}
+
+__device__ __forceinline__ float2 soft(float2 u, float kappa) {
+  const float mag = sqrtf(u.x * u.x + u.y * u.y);
+  const float s = (mag > kappa) ? (1.f - kappa / mag) : 0.f;
+  return make_float2(u.x * s, u.y * s);
+}
+
+
+// FISTA scalars after the finalize of iteration k, from the restart inner
+// product Re<y_k - x_k, x_k - x_{k-1}> (O'Donoghue-Candes gradient restart):
+// t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, or 1 on restart; beta for the next
+// extrapolation from t_{k+1} and t_{k+2}.
+__device__ __forceinline__ void fista_update(DevScalars* sc, double dot) {
+  sc->restart_dot = dot;
+  if (!isfinite(dot)) sc->nonfinite = 1;
+  double t = sc->t;
+  int restart = 0;
+  if (sc->accelerate) {
+    double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    if (sc->restart && dot > 0.0) {
+      tn = 1.0;
+      restart = 1;
+    }
+    t = tn;
+    const double t2 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc->beta = (t - 1.0) / t2;
+  } else {
+    t = 1.0;
+    sc->beta = 0.0;
+  }
+  sc->t = t;
+  sc->restart_flag = restart;
+}
+
+constexpr int TX2 = kTv2Tx;
+template <int NW>
+struct TvLayout2 {   // two dual steps per launch, NW warps (one per halo row)
+  static constexpr int kSlot = slot_bytes(kTv2BoxW, NW + 1);
+  static constexpr int kXOff = kTv2Stages * 4 * kSlot;
   // exchange rows for y-neighbours (one pair of complex values per lane),
-  // double buffered by plane parity: u0 [2][NW2][32], p1_y [2][NW2][32], u1 [2][NW2][32]
-  static constexpr int kXRow = NW2 * 32 * 16;
-  static constexpr int kBarOffset = kXOff + 6 * kXRow;
+  // double buffered by plane parity: u0, p1_y, u1 and (fused finalize) p2_y,
+  // each [2][NW][32]
+  static constexpr int kXRow = NW * 32 * 16;
+  static constexpr int kBarOffset = kXOff + 8 * kXRow;
   static constexpr int kBytes = kBarOffset + kTv2Stages * 8;
 };
 
@@ -349,26 +429,45 @@ __device__ __forceinline__ float4 pack4(float2 a, float2 b) { return make_float4
 // region compute values that no output uses; every use is guarded by the same
 // global-index boundary conditions as the single step. Needs nx even (pairs
 // of outputs are stored as 16-byte words).
-template <bool FIRST>
-__global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_constant__ TvArgs a) {
+//
+// FINAL (the last launch of a prox): the tile is 58 x 11 (15 warps) and the
+// halo one voxel wider on the low sides (x = i0-4+2l+e, y = j0-2+w, one more
+// plane before the chunk), so that p^2 is known at x-1, y-1 and z-1 of every
+// tile voxel; after a second barrier per tick,
+//   (e) x(t-1) = soft(v - mu D^H p^2, kappa)   [p^2(t-1), p^2_z(t-2)]
+// is written instead of p^2, in FISTA mode with y_{k+1} = x + beta (x -
+// x_prev) and the restart inner product, reduced like the finalize kernel.
+template <bool FIRST, bool FINAL, int FMODE = FIN_PROX>
+__global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
+    k_tv_step2(const __grid_constant__ TvArgs a) {
+  constexpr bool FISTA = FINAL && FMODE == FIN_FISTA;
+  constexpr int TXk = FINAL ? kTv2TxF : kTv2Tx;
+  constexpr int TYk = FINAL ? kTv2TyF : kTv2Ty;
+  constexpr int NW2 = FINAL ? kTv2WarpsF : kTv2Warps;
+  using Layout = TvLayout2<NW2>;
+  constexpr int X0 = FINAL ? 4 : 2;    // box and lane 0 start at x = i0 - X0
+  constexpr int Y0 = FINAL ? 3 : 2;    // box starts at y = j0 - Y0, warp 0 at j0 - Y0 + 1
+  constexpr int L = FINAL ? 1 : 0;     // extra planes of z halo before the chunk
+  using Ring = PlaneRing<kTv2BoxW, NW2 + 1, Y0, kTv2Stages, X0>;
   extern __shared__ __align__(128) unsigned char smem[];
   using Row = float4[NW2][32];
   using Box4 = const float4(*)[kTv2BoxW / 2];
-  Row* XU0 = reinterpret_cast<Row*>(smem + TvLayout2::kXOff);
+  Row* XU0 = reinterpret_cast<Row*>(smem + Layout::kXOff);
   Row* XP1 = XU0 + 2;
   Row* XU1 = XU0 + 4;
+  Row* XP2 = XU0 + 6;                           // FINAL only
   const int zc0 = blockIdx.z * a.zchunk;
   const int zc1 = min(a.nz, zc0 + a.zchunk);
-  Ring2 ring{smem, reinterpret_cast<unsigned long long*>(smem + TvLayout2::kBarOffset), zc0 - 2};
-  const int i0 = blockIdx.x * TX2, j0 = blockIdx.y * kTv2Ty;
+  Ring ring{smem, reinterpret_cast<unsigned long long*>(smem + Layout::kBarOffset), zc0 - 2 - L};
+  const int i0 = blockIdx.x * TXk, j0 = blockIdx.y * TYk;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int gx0 = i0 - 2 + 2 * lane, gy = j0 - 1 + w;   // element e at x = gx0 + e
+  const int gx0 = i0 - X0 + 2 * lane, gy = j0 - (Y0 - 1) + w;   // element e at x = gx0 + e
   const int by = w + 1;                                 // own row in the box
   const int cm = lane > 0 ? 2 * lane - 1 : 0;           // box column x-1 of element 0
   const int ln = lane < 31 ? lane + 1 : lane;           // next lane (x+1 of element 1)
   const int qlast = zc1 + 1;
-  const bool out_pair = w >= 1 && w <= kTv2Ty && lane >= 1 && lane <= TX2 / 2 && gx0 < a.nx &&
-                        gy < a.ny;
+  const bool out_pair = w >= Y0 - 1 && w <= Y0 - 2 + TYk && lane >= X0 / 2 &&
+                        lane <= (TXk + X0 - 2) / 2 && gx0 < a.nx && gy < a.ny;
   const int wn = w + 1 < NW2 ? w + 1 : w;       // y+1 row (the last row's value is unused)
   const int wp = w >= 1 ? w - 1 : w;            // y-1 row (the first row's value is unused)
   // Boundary conditions as multipliers, so that every term is one packed
@@ -406,18 +505,24 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
   float2 p1_prev[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};
   float2 p1_t[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};
   float2 u1_prev[2] = {zero, zero}, u1_t[2] = {zero, zero};
+  // FINAL: v of plane t-1 and p^2_z of plane t-2; FISTA restart partials
+  float2 v_prev[2] = {zero, zero}, p2z_prev[2] = {zero, zero};
+  float dot_local = 0.f;
+  double dot_sum = 0.0;
+  int dot_cnt = 0;
+  const float beta = FISTA ? static_cast<float>(a.sc->beta) : 0.f;
 
-  // prologue: p^0_z of plane zc0-2 (read by u^0(zc0-1))
-  if (!ring_wait(ring, zc0 - 2)) { ring_abort(ring, a, waited, issued); return; }
-  waited = zc0 - 2;
+  // prologue: p^0_z of the ring's first plane (read by u^0 of the next)
+  if (!ring_wait(ring, ring.base)) { ring_abort(ring, a, waited, issued); return; }
+  waited = ring.base;
   if (!FIRST && a.dims == 3) {
-    const float4 pz = reinterpret_cast<Box4>(ring.slot(zc0 - 2, 3))[by][lane];
+    const float4 pz = reinterpret_cast<Box4>(ring.slot(ring.base, 3))[by][lane];
     p0_t[2][0] = lo2(pz);
     p0_t[2][1] = hi2(pz);
   }
   __syncthreads();
 
-  for (int t = zc0 - 2; t <= zc1; ++t) {
+  for (int t = ring.base; t <= zc1; ++t) {
     // plane t was last read in tick t-1, before that tick's barrier: refill
     // its stage with plane t+NS
     if (t + kTv2Stages <= qlast) {
@@ -426,6 +531,14 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
         ring_issue<FIRST>(ring, a, t + kTv2Stages, i0, j0);
       }
       issued = t + kTv2Stages;
+    }
+    // FINAL + FISTA: x_{k-1} and y_k of plane t-1 are loaded now, a whole
+    // tick before step (e) uses them
+    float4 xp4 = make_float4(0.f, 0.f, 0.f, 0.f), yk4 = xp4;
+    if (FISTA && t >= zc0 + 1 && out_pair) {
+      const size_t gidx = (static_cast<size_t>(t - 1) * a.ny + gy) * a.nx + gx0;
+      xp4 = *reinterpret_cast<const float4*>(a.x_prev + gidx);
+      yk4 = *reinterpret_cast<const float4*>(a.y + gidx);
     }
     // (a) u^0(t+1) from the box of plane t+1 (the wait is voted on below)
     const int q = t + 1;
@@ -474,7 +587,7 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
       XU0[q & 1][w][lane] = pack4(u0_n[0], u0_n[1]);
     }
     // (b) p^1(t)
-    if (t >= zc0 - 1) {
+    if (t >= zc0 - 1 - L) {
       const float2 ux[2] = {u0_t[1], lo2(XU0[t & 1][w][ln])};
       const float4 uy4 = XU0[t & 1][wn][lane];
       const float2 uy[2] = {lo2(uy4), hi2(uy4)};
@@ -491,7 +604,8 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
     if (!__syncthreads_and(ok)) { ring_abort(ring, a, waited, issued); return; }
     waited = q;
     // (c) u^1(t)
-    if (t >= zc0) {
+    float2 qo[3][2] = {{zero, zero}, {zero, zero}, {zero, zero}};   // p^2(t-1)
+    if (t >= zc0 - L) {
       const float2 pxm[2] = {shfl_up2(p1_t[0][1]), p1_t[0][0]};
       const float4 pym4 = XP1[t & 1][wp][lane];
       const float2 pym[2] = {lo2(pym4), hi2(pym4)};
@@ -511,12 +625,11 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
       }
       XU1[t & 1][w][lane] = pack4(u1_t[0], u1_t[1]);
       // (d) p^2(t-1)
-      if (t >= zc0 + 1) {
+      if (t >= zc0 + 1 - L) {
         const float2 ux[2] = {u1_prev[1], lo2(XU1[(t - 1) & 1][w][ln])};
         const float4 uy4 = XU1[(t - 1) & 1][wn][lane];
         const float2 uy[2] = {lo2(uy4), hi2(uy4)};
         const float2 szhi = splat(a.dims == 3 && t - 1 <= a.nz - 2 ? a.step : 0.f);
-        float2 qo[3][2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           qo[0][e] = x2fma(e == 0 ? stp : sxhi1, x2sub(ux[e], u1_prev[e]), p1_prev[0][e]);
@@ -524,12 +637,61 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
           qo[2][e] = x2fma(szhi, x2sub(u1_t[e], u1_prev[e]), p1_prev[2][e]);
           project2(qo[0][e], qo[1][e], qo[2][e]);
         }
-        if (out_pair) {
+        if (FINAL) {
+          XP2[(t - 1) & 1][w][lane] = pack4(qo[1][0], qo[1][1]);
+        } else if (out_pair) {
           const size_t gidx = (static_cast<size_t>(t - 1) * a.ny + gy) * a.nx + gx0;
           *reinterpret_cast<float4*>(a.pout[0] + gidx) = pack4(qo[0][0], qo[0][1]);
           *reinterpret_cast<float4*>(a.pout[1] + gidx) = pack4(qo[1][0], qo[1][1]);
           if (a.dims == 3) *reinterpret_cast<float4*>(a.pout[2] + gidx) = pack4(qo[2][0], qo[2][1]);
         }
+      }
+    }
+    if constexpr (FINAL) {
+      __syncthreads();
+      // (e) x(t-1) = soft(v - mu D^H p^2, kappa)
+      if (t >= zc0 + 1) {
+        const int qf = t - 1;
+        const float2 pxm[2] = {shfl_up2(qo[0][1]), qo[0][0]};
+        const float4 pym4 = XP2[(t - 1) & 1][wp][lane];
+        const float2 pym[2] = {lo2(pym4), hi2(pym4)};
+        const float2 mzlo = splat(a.dims == 3 && qf >= 1 ? 1.f : 0.f);
+        const float2 mzhi = splat(a.dims == 3 && qf <= a.nz - 2 ? -1.f : 0.f);
+        float2 xv[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float2 dh = e == 0 ? x2mul(mxlo0, pxm[0]) : pxm[1];
+          dh = e == 0 ? x2sub(dh, qo[0][0]) : x2fma(mxhi1, qo[0][1], dh);
+          dh = x2fma(mylo, pym[e], dh);
+          dh = x2fma(myhi, qo[1][e], dh);
+          if (a.dims == 3) {
+            dh = x2fma(mzlo, p2z_prev[e], dh);
+            dh = x2fma(mzhi, qo[2][e], dh);
+          }
+          xv[e] = soft_rsqrt(x2fma(nmu, dh, v_prev[e]), a.kappa);
+        }
+        if (out_pair) {
+          const size_t gidx = (static_cast<size_t>(qf) * a.ny + gy) * a.nx + gx0;
+          if (FISTA) {
+            const float2 xp[2] = {lo2(xp4), hi2(xp4)};
+            const float2 yk[2] = {lo2(yk4), hi2(yk4)};
+            float2 yo[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float2 dx = csub(xv[e], xp[e]);
+              dot_local += (yk[e].x - xv[e].x) * dx.x + (yk[e].y - xv[e].y) * dx.y;
+              yo[e] = make_float2(xv[e].x + beta * dx.x, xv[e].y + beta * dx.y);
+            }
+            if (++dot_cnt == 4) { dot_sum += dot_local; dot_local = 0.f; dot_cnt = 0; }
+            *reinterpret_cast<float4*>(a.y_out + gidx) = pack4(yo[0], yo[1]);
+          }
+          *reinterpret_cast<float4*>(a.x_out + gidx) = pack4(xv[0], xv[1]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        p2z_prev[e] = qo[2][e];
+        v_prev[e] = v_t[e];
       }
     }
     // rotate the per-position state to the next plane
@@ -545,45 +707,30 @@ __global__ void __launch_bounds__(kTv2Threads, 1) k_tv_step2(const __grid_consta
       }
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// Reductions
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (wid == 0) {
-    r = (lane < static_cast<int>(blockDim.x >> 5)) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-  }
-  __syncthreads();
-  return r;
-}
-
-// Writes this block's partial (slot `which`) and returns true in every thread
-// of the last block to arrive, which then owns the final sum.
-__device__ __forceinline__ bool publish_partial(double bs, RedWork w, int which, int ticket) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    w.partials[which * kRedBlocks + blockIdx.x] = bs;
+  if (FISTA) {
+    // restart inner product: FP32 over at most 8 voxels, FP64 above; fixed-
+    // order sum over the CTAs by the last one, which updates t and beta
+    dot_sum += dot_local;
+    const double bs = block_sum(dot_sum);
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    __shared__ bool last;
+    if (tid == 0) {
+      a.fin_partials[bid] = bs;
+      __threadfence();
+      last = atomicAdd(a.fin_ticket, 1u) == static_cast<unsigned>(nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
     __threadfence();
-    last = atomicAdd(&w.tickets[ticket], 1u) == gridDim.x - 1;
+    double v = 0.0;
+    for (int b = tid; b < nblk; b += blockDim.x) v += static_cast<volatile double*>(a.fin_partials)[b];
+    const double dot = block_sum(v);
+    if (tid == 0) {
+      fista_update(a.sc, dot);
+      *a.fin_ticket = 0;
+    }
   }
-  __syncthreads();
-  return last;
-}
-
-__device__ __forceinline__ double final_sum(RedWork w, int which) {
-  __threadfence();
-  double v = 0.0;
-  for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
-    v += static_cast<volatile double*>(w.partials)[which * kRedBlocks + b];
-  return block_sum(v);
 }
 
 // u = v - mu D^H p at voxel (i, j, k), straight from global memory.
@@ -603,12 +750,6 @@ __device__ __forceinline__ float2 form_u(const FinArgs& a, size_t idx, int i, in
     u = make_float2(u.x - a.mu * dh.x, u.y - a.mu * dh.y);
   }
   return u;
-}
-
-__device__ __forceinline__ float2 soft(float2 u, float kappa) {
-  const float mag = sqrtf(u.x * u.x + u.y * u.y);
-  const float s = (mag > kappa) ? (1.f - kappa / mag) : 0.f;
-  return make_float2(u.x * s, u.y * s);
 }
 
 template <int MODE>
@@ -641,26 +782,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const __grid_constant_
   if (!publish_partial(bs, a.w, 0, 1)) return;
   const double dot = final_sum(a.w, 0);
   if (threadIdx.x == 0) {
-    DevScalars* sc = a.sc;
-    sc->restart_dot = dot;
-    if (!isfinite(dot)) sc->nonfinite = 1;
-    double t = sc->t;
-    int restart = 0;
-    if (sc->accelerate) {
-      double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      if (sc->restart && dot > 0.0) {
-        tn = 1.0;
-        restart = 1;
-      }
-      t = tn;
-      const double t2 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      sc->beta = (t - 1.0) / t2;
-    } else {
-      t = 1.0;
-      sc->beta = 0.0;
-    }
-    sc->t = t;
-    sc->restart_flag = restart;
+    fista_update(a.sc, dot);
     a.w.tickets[1] = 0;
   }
 }
@@ -740,11 +862,12 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
-int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms) {
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final) {
   if (nsteps != 2) return 32;
   // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks. Pick the
   // chunk that minimises (waves, rounded up) x (ticks per chunk).
-  const long tiles = static_cast<long>((nx + TX2 - 1) / TX2) * ((ny + kTv2Ty - 1) / kTv2Ty);
+  const int tx = final ? kTv2TxF : TX2, ty = final ? kTv2TyF : kTv2Ty;
+  const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
   int best = 32;
   long best_cost = -1;
   for (int zc : {16, 32, 64, 128, 256}) {
@@ -760,19 +883,30 @@ int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms) {
   return best;
 }
 
-cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s) {
+cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s, bool final) {
   if (nsteps == 2 && (a.nx & 1)) return cudaErrorInvalidValue;   // pairs of x positions
-  const int tx = nsteps == 2 ? TX2 : TX;
-  const int ty = nsteps == 2 ? kTv2Ty : TY;
+  if (final && nsteps != 2) return cudaErrorInvalidValue;
+  const int tx = nsteps == 2 ? (final ? kTv2TxF : TX2) : TX;
+  const int ty = nsteps == 2 ? (final ? kTv2TyF : kTv2Ty) : TY;
   dim3 grid((a.nx + tx - 1) / tx, (a.ny + ty - 1) / ty, (a.nz + a.zchunk - 1) / a.zchunk);
-  auto kern = nsteps == 2 ? (first ? k_tv_step2<true> : k_tv_step2<false>)
-                          : (first ? k_tv_step<true> : k_tv_step<false>);
-  const int bytes = nsteps == 2 ? TvLayout2::kBytes : TvLayout1::kBytes;
-  const int threads = nsteps == 2 ? kTv2Threads : kTvThreads;
+  const bool fista = a.fin_mode == FIN_FISTA;
+  auto kern = nsteps == 2
+                  ? (final ? (fista ? (first ? k_tv_step2<true, true, FIN_FISTA>
+                                             : k_tv_step2<false, true, FIN_FISTA>)
+                                    : (first ? k_tv_step2<true, true> : k_tv_step2<false, true>))
+                           : (first ? k_tv_step2<true, false> : k_tv_step2<false, false>))
+                  : (first ? k_tv_step<true> : k_tv_step<false>);
+  const int bytes = nsteps == 2 ? (final ? TvLayout2<kTv2WarpsF>::kBytes : TvLayout2<kTv2Warps>::kBytes)
+                                : TvLayout1::kBytes;
+  const int threads = nsteps == 2 ? 32 * (final ? kTv2WarpsF : kTv2Warps) : kTvThreads;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   kern<<<grid, threads, bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
+  return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
 }
 
 // 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box

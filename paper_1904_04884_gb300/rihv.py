@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tv_dims", ctypes.c_int), ("restart", ctypes.c_int),
                 ("accelerate", ctypes.c_int), ("n_inner", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
-                ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int)]
+                ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int),
+                ("fuse_finalize", ctypes.c_int)]
 
 
 class Particle(ctypes.Structure):

@@ -110,6 +110,48 @@ def test_prox_parity(nx, ny, nz, k, dims, per_launch):
     assert rel_l2(out.cpu().numpy(), ref) <= OP_TOL
 
 
+@pytest.mark.parametrize("dims", [3, 2])
+@pytest.mark.parametrize("nx,ny,nz,k", [(96, 48, 37, 4), (64, 32, 5, 2), (192, 48, 33, 6)])
+def test_fused_finalize_prox_matches_oracle_and_separate(nx, ny, nz, k, dims):
+    """The last two-step launch forms x = soft(v - mu D^H p) itself (tile 58 x
+    15, one more halo ring): same result as the separate finalize kernel and
+    the oracle's prox, including ragged tiles and z-chunks."""
+    op = optics(nx, ny, nz)
+    v = synth.random_complex(synth.Stream(nz * 7 + k + dims), op.shape)
+    h = handle(op)
+    outs = {}
+    for fuse in (1, 0):
+        h.set_options(tv_dims=dims, tv_steps_per_launch=2, fuse_finalize=fuse)
+        out = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+        h.prox_fused_lasso(to_dev(v), 0.3, 0.05, k, out)
+        torch.cuda.synchronize()
+        outs[fuse] = out.cpu().numpy()
+    ref = O.prox_fused_lasso(v, 0.3, 0.05, k, dims)
+    assert rel_l2(outs[1], ref) <= OP_TOL
+    assert rel_l2(outs[1], outs[0]) <= OP_TOL
+
+
+def test_fused_finalize_fista_matches_separate():
+    """FISTA iterations with the fused finalize (x, y_{k+1}, restart product and
+    the t / beta update on the device) follow the separate-kernel path."""
+    op = optics(96, 64, 19)
+    x_true = np.zeros(op.shape, np.complex128)
+    x_true[9, 20:24, 30:34] = 1.0
+    x_true[4, 40:43, 70:73] = 0.7
+    b = synth.intensity_hologram(O.forward(x_true, op), 0.01, synth.Stream(5).normal(op.nx * op.ny))
+    res = {}
+    for fuse in (1, 0):
+        h = handle(op)
+        h.set_options(n_inner=6, check_every=5, tv_steps_per_launch=2, fuse_finalize=fuse)
+        x = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+        tr = np.zeros(6)
+        h.solve(b.astype(np.float32), 0.01, 0.005, 30, x, trace=tr)
+        torch.cuda.synchronize()
+        res[fuse] = (x.cpu().numpy(), tr)
+    assert rel_l2(res[1][0], res[0][0]) <= 1e-4
+    assert np.allclose(res[1][1], res[0][1], rtol=1e-5)
+
+
 def test_prox_soft_threshold_only_and_identity():
     op = optics(32, 16, 4)
     v = synth.random_complex(synth.Stream(9), op.shape)
