@@ -119,15 +119,16 @@ def kernel_hash():
 
 
 def measured_traffic(nvox, kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to this workload, or None when the kernel changed since it was captured."""
+    """DRAM bytes per launch of `kernel` (its launches reading p) from the
+    committed ncu summary, scaled to this workload, or None when the kernel
+    changed since it was captured."""
     try:
         prof = json.load(open(TV_PROFILE))
     except Exception:
         return None
     if prof.get("kernel_hash") != kernel_hash() or prof.get("kernel_name") != kernel:
         return None
-    return prof["dram_bytes_per_voxel_per_launch"] * nvox
+    return prof["launch_kinds"]["tv_mid"]["dram_bytes_per_voxel"] * nvox
 
 
 def hbm_peak():
@@ -307,7 +308,11 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     ndet = 0
-    for _ in range(args.steps):
+    for i in range(args.steps):
+        # per-launch TV events (level 2) only in the last timed step: they put
+        # a small gap between launches, so the other steps run without them
+        if i == args.steps - 1:
+            h.set_profiling(2)
         ndet = len(step_device())
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -348,23 +353,31 @@ def main():
     value = vox_iters * args.steps * world / (ms / 1e3)
     e2e_value = vox_iters * e2e_steps * world / (e2e_ms / 1e3)
 
-    # roofline of the TV dual-step kernel, from the live stage events
-    tv_kernel = "k_tv_step2" if h.options.tv_steps_per_launch == 2 else "k_tv_step"
-    tv_ms, tv_launches = stages["tv"]
-    # 32 B/voxel for the launch that starts from p = 0 (reads v, writes p),
-    # 56 B/voxel for every other launch (reads v and p, writes p), whatever
-    # number of dual steps a launch performs; the last launch with the fused
-    # finalize reads v and p and x_{k-1}, y_k and writes x_k, y_{k+1} instead
-    # of p: 64 B/voxel.
-    per_prox = tv_launches // (args.steps * (w.iters + 0)) if tv_launches else 1
-    fused = (h.options.tv_steps_per_launch == 2 and h.options.fuse_finalize == 1
-             and w.n_inner % 2 == 0 and per_prox >= 2)
-    alg = 32 + 56 * (per_prox - 1) + (64 - 56 if fused else 0)
-    alg_bytes_per_launch = w.nvox * alg / max(per_prox, 1)
-    avg_launch_s = (tv_ms / 1e3) / max(tv_launches, 1)
-    achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if tv_launches else None
+    # Roofline of the dominant kernel, the TV launch that reads p (two dual
+    # steps per launch by default), from the per-launch CUDA events the
+    # library records on its stream during the last timed step. Algorithmic bytes
+    # per voxel by launch kind: 56 reading p (read v and p, write p), 32 for
+    # the first launch of a prox (p = 0: read v, write p), 64 for the last
+    # launch with the fused finalize (read v, p, x_{k-1}, y_k; write x_k and
+    # y_{k+1} instead of p).
+    per = h.options.tv_steps_per_launch
+    tv_kernel = "k_tv_step2" if per == 2 else "k_tv_step"
     peak, peak_kind = hbm_peak()
-    total_launches = sum(n for _, n in stages.values())
+    kinds = {}
+    for kind, alg in (("tv_first", 32), ("tv_mid", 56), ("tv_final", 64)):
+        kms, kn = stages[kind]
+        kn = kn / args.steps         # launches are counted in every step, timed in the last
+        if kn:
+            avg_s = kms / 1e3 / kn
+            ach = w.nvox * alg / avg_s / 1e9
+            kinds[kind] = {"launches_timed": kn, "avg_launch_ms": avg_s * 1e3,
+                           "alg_bytes_per_voxel": alg, "achieved_gbs": ach, "frac": ach / peak}
+    dom = kinds.get("tv_mid") or kinds.get("tv_first")
+    achieved = dom["achieved_gbs"] if dom else None
+    alg_bytes_per_launch = w.nvox * (dom["alg_bytes_per_voxel"] if dom else 0)
+    avg_launch_s = dom["avg_launch_ms"] / 1e3 if dom else 0.0
+    main_stages = ("forward", "adjoint", "tv", "finalize", "objective", "detect", "setup")
+    total_launches = sum(stages[k][1] for k in main_stages)
 
     ttt = None
     if not args.no_warmstart:
@@ -391,15 +404,15 @@ def main():
                 "h2d_bytes_per_step": int(w.nx * w.ny * 4),
                 "d2h_bytes_per_step": int(w.nvox * 8 + (w.iters // 10) * 8)},
         "gpu_launches": int(total_launches),
-        "roofline": {"bound": "hbm", "kernel": tv_kernel, "achieved": achieved,
-                     "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": tv_kernel + " (launch reading p)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": measured_traffic(w.nvox, tv_kernel), "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes_per_launch,
-                     "dual_steps_per_launch": h.options.tv_steps_per_launch,
-                     "fused_finalize": bool(fused),
-                     "avg_launch_ms": avg_launch_s * 1e3},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                     "dual_steps_per_launch": per,
+                     "avg_launch_ms": avg_launch_s * 1e3,
+                     "tv_launch_kinds": kinds},
+        "stages_ms_per_step": {k: stages[k][0] / args.steps for k in main_stages},
         "time_to_tolerance": ttt,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -215,14 +215,20 @@ rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out, int nx, in
                                           int tv_dims, float t_l1, float t_tv, int inner_iters,
                                           void* stream);
 
-/* Per-stage timing. Kernel launches are always counted per stage. When
- * profiling is on, the library also records CUDA events around its stages on
- * the handle's stream. rihv_stage_times returns accumulated milliseconds (0
+/* Per-stage timing. Kernel launches are always counted per stage. With
+ * profiling level 1 (rihv_set_profiling(h, 1)) the library also records CUDA
+ * events around its stages on the handle's stream; level 2 adds events around
+ * every TV launch (stages 7-9), which costs a little time: an event between
+ * two launches keeps the second from starting while the first drains. rihv_stage_times returns accumulated milliseconds (0
  * without profiling) and launch counts per stage, after synchronising the
  * stream, and resets both. Stages, in order: 0 forward, 1 adjoint + gradient
  * step, 2 TV dual steps, 3 finalize (soft threshold, momentum, restart),
- * 4 objective, 5 detection, 6 solve set-up (hologram spectrum, x_0, scalars).
- * n is the capacity of both arrays (up to 7 are written); either may be NULL. */
+ * 4 objective, 5 detection, 6 solve set-up (hologram spectrum, x_0, scalars);
+ * then the TV launches of stage 2 by kind (one scope per launch, counted in
+ * stage 2 too): 7 the first launch of a prox (p = 0), 8 launches reading p,
+ * 9 the last launch with the fused finalize (its finalize is not in stage 3).
+ * n is the capacity of both arrays (up to 10 are written); either may be
+ * NULL. */
 rihv_status rihv_set_profiling(rihv_handle h, int on);
 rihv_status rihv_stage_times(rihv_handle h, double* ms, long long* launches, int n);
 

@@ -21,12 +21,15 @@ namespace {
 
 thread_local std::string g_last_error;
 
-constexpr int kNumStages = 7;
+constexpr int kNumStages = 10;
 enum Stage {
   ST_FORWARD = 0, ST_ADJOINT = 1, ST_TV = 2, ST_FINAL = 3, ST_OBJECTIVE = 4, ST_DETECT = 5,
-  ST_SETUP = 6
+  ST_SETUP = 6,
+  // sub-stages of ST_TV, one scope per launch: starting from p = 0, reading
+  // p, and the launch with the fused finalize
+  ST_TV_FIRST = 7, ST_TV_MID = 8, ST_TV_FINAL = 9
 };
-constexpr int kEventPool = 8192;
+constexpr int kEventPool = 65536;   // two per stage scope; a full pool flushes (synchronises)
 
 bool supported_n(int n) {
   if (n < 16 || n > kMaxN) return false;
@@ -104,7 +107,7 @@ struct rihv_ctx {
   std::vector<void*> allocs;
 
   // profiling
-  bool prof = false;
+  int prof = 0;                      // 0 off, 1 stage events, 2 also per TV launch
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   struct Rec { int stage; int launches; cudaEvent_t a, b; };
@@ -197,15 +200,19 @@ struct StageScope {
   int stage;
   int launches;
   cudaEvent_t a = nullptr;
-  StageScope(rihv_ctx* hh, int st, int nl) : h(hh), stage(st), launches(nl) {
+  // min_level: the profiling level at which this scope records events (the
+  // per-launch TV scopes only at level 2: an event between two launches keeps
+  // the second from starting while the first drains)
+  StageScope(rihv_ctx* hh, int st, int nl, int min_level = 1)
+      : h(hh), stage(st), launches(nl) {
     h->stage_launches[stage] += launches;
-    if (!h->prof) return;
+    if (h->prof < min_level) return;
     if (h->ev_used + 2 > h->ev_pool.size()) flush();
     a = h->ev_pool[h->ev_used++];
     cudaEventRecord(a, h->stream);
   }
   ~StageScope() {
-    if (!h->prof || !a) return;
+    if (!a) return;
     cudaEvent_t b = h->ev_pool[h->ev_used++];
     cudaEventRecord(b, h->stream);
     h->recs.push_back({stage, 0, a, b});
@@ -338,7 +345,10 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
       a.tm_p[c] = src_is_b ? h->tm_pb[b][c] : h->tm_pa[b][c];
       a.pout[c] = dst[c];
     }
-    CK(launch_tv_step(done == 0, n, a, h->stream, fused && last));
+    {
+      StageScope sub(h, (fused && last) ? ST_TV_FINAL : (done == 0 ? ST_TV_FIRST : ST_TV_MID), 1, 2);
+      CK(launch_tv_step(done == 0, n, a, h->stream, fused && last));
+    }
     done += n;
     std::swap(src, dst);
     src_is_b = !src_is_b;
@@ -810,7 +820,7 @@ rihv_status rihv_set_profiling(rihv_handle h, int on) {
     h->ev_pool.resize(kEventPool);
     for (auto& e : h->ev_pool) CK(cudaEventCreate(&e));
   }
-  h->prof = on != 0;
+  h->prof = on < 0 ? 0 : (on > 2 ? 2 : on);
   return RIHV_OK;
 }
 
@@ -889,7 +899,7 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     b->exec = nullptr;
   }
   std::vector<cudaStream_t> saved(n);
-  std::vector<bool> saved_prof(n);
+  std::vector<int> saved_prof(n);
   b->launches.assign(n, std::vector<long long>(kNumStages, 0));
   b->checks.assign(n, 0);
   rihv_ctx* h0 = b->hs[0];
@@ -902,7 +912,7 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     saved[i] = h->stream;
     saved_prof[i] = h->prof;
     h->stream = b->branch[i];
-    h->prof = false;
+    h->prof = 0;
     long long before[kNumStages];
     for (int s = 0; s < kNumStages; ++s) before[s] = h->stage_launches[s];
     cudaStreamWaitEvent(b->branch[i], b->fork, 0);
@@ -1052,8 +1062,8 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     CK(cudaMemsetAsync(h->v, 0, h->nvox * sizeof(float2), h->stream));
     CK(cudaMemsetAsync(h->y, 0, h->nvox * sizeof(float2), h->stream));
     CK(cudaMemsetAsync(h->spec, 0, h->nxy * sizeof(float2), h->stream));
-    const bool prof = h->prof;
-    h->prof = false;
+    const int prof = h->prof;
+    h->prof = 0;
     const rihv_options saved = h->opt;
     const int saved_zc = h->tv_zchunk, saved_zpg = h->zpg, saved_g = h->groups;
     rihv_status st = RIHV_OK;

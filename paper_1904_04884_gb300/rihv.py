@@ -27,7 +27,8 @@ EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stre
            "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
            "rihv_batch_destroy", "rihv_autotune"]
 
-STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup"]
+STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup",
+          "tv_first", "tv_mid", "tv_final"]
 
 
 class RihvError(RuntimeError):
@@ -231,14 +232,16 @@ class Rihv:
     autotune = rihv_autotune
 
     # -- profiling ----------------------------------------------------------
-    def set_profiling(self, on: bool):
-        self._check(self.L.rihv_set_profiling(self.h, 1 if on else 0), self.h)
+    def set_profiling(self, on):
+        """False/0 off; True/1 stage events; 2 also events around every TV launch."""
+        self._check(self.L.rihv_set_profiling(self.h, int(on)), self.h)
 
     def stage_times(self):
         """{stage: (ms, launches)} accumulated since the last call."""
-        ms = (ctypes.c_double * 7)()
-        nl = (ctypes.c_longlong * 7)()
-        self._check(self.L.rihv_stage_times(self.h, ms, nl, 7), self.h)
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        nl = (ctypes.c_longlong * n)()
+        self._check(self.L.rihv_stage_times(self.h, ms, nl, n), self.h)
         return {s: (ms[i], nl[i]) for i, s in enumerate(STAGES)}
 
     # short aliases
