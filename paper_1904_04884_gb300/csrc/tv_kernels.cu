@@ -305,11 +305,19 @@ __device__ __forceinline__ double final_sum(RedWork w, int which) {
   return block_sum(v);
 }
 
-// The same shrinkage through the reciprocal square root (one hardware
-// approximation instead of a square root and a division; 2 ulp).
+// Reciprocal square root by the hardware approximation (PTX rsqrt.approx,
+// relative error below 2^-22; inputs here are > 1 or > kappa^2, never
+// subnormal, so flushing subnormals changes nothing).
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// The shrinkage through the reciprocal square root (one hardware
+// approximation instead of a square root and a division).
 __device__ __forceinline__ float2 soft_rsqrt(float2 u, float kappa) {
   const float m2 = u.x * u.x + u.y * u.y;
-  const float s = (m2 > kappa * kappa) ? (1.f - kappa * rsqrtf(m2)) : 0.f;
+  const float s = (m2 > kappa * kappa) ? (1.f - kappa * rsqrt_hw(m2)) : 0.f;
   return make_float2(u.x * s, u.y * s);
 }
 
@@ -393,7 +401,7 @@ __device__ __forceinline__ float2 x2fma(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ void project2(float2& qx, float2& qy, float2& qz) {
   const float2 s = x2fma(qz, qz, x2fma(qy, qy, x2mul(qx, qx)));
   const float n2 = s.x + s.y;
-  const float r = n2 > 1.f ? rsqrtf(n2) : 1.f;
+  const float r = n2 > 1.f ? rsqrt_hw(n2) : 1.f;
   const float2 sc = make_float2(r, r);
   qx = x2mul(qx, sc);
   qy = x2mul(qy, sc);
