@@ -376,3 +376,39 @@ def coo_bytes(nnz: int) -> int:
 def coo_break_even_sparsity() -> float:
     """Sparsity (zero fraction) above which COO storage is smaller than dense."""
     return 1.0 - 8.0 / 24.0
+
+
+# --------------------------------------------------------------------------
+# Per-plane COO storage (Section 2, GPU implementation paragraph)
+# --------------------------------------------------------------------------
+
+def coo_compact(x: np.ndarray):
+    """Per-plane coordinate (COO) form of a volume x [nz][ny][nx]: every plane
+    indexes its own non-zero elements (row j, column i, value), as the paper
+    stores volumes plane by plane. Returns (plane_offsets int64 [nz+1], rows,
+    cols, vals) with plane k's entries at [plane_offsets[k], plane_offsets[k+1])
+    in row-major order (j, then i). An element is non-zero unless both its
+    real and imaginary parts equal zero."""
+    x = np.asarray(x)
+    nz = x.shape[0]
+    offsets = np.zeros(nz + 1, np.int64)
+    rows, cols, vals = [], [], []
+    for k in range(nz):
+        plane = x[k]
+        nzmask = (plane.real != 0) | (plane.imag != 0)
+        j, i = np.nonzero(nzmask)          # row-major order
+        rows.append(j)
+        cols.append(i)
+        vals.append(plane[j, i])
+        offsets[k + 1] = offsets[k] + len(j)
+    return (offsets, np.concatenate(rows).astype(np.int64), np.concatenate(cols).astype(np.int64),
+            np.concatenate(vals) if vals else np.zeros(0, x.dtype))
+
+
+def coo_expand(offsets, rows, cols, vals, shape, dtype=np.complex128) -> np.ndarray:
+    """Dense volume from its per-plane COO form (zeros elsewhere)."""
+    x = np.zeros(shape, dtype)
+    for k in range(shape[0]):
+        a, b = int(offsets[k]), int(offsets[k + 1])
+        x[k, rows[a:b], cols[a:b]] = vals[a:b]
+    return x
