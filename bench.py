@@ -379,6 +379,21 @@ def main():
     main_stages = ("forward", "adjoint", "tv", "finalize", "objective", "detect", "setup")
     total_launches = sum(stages[k][1] for k in main_stages)
 
+    # per-plane COO form of the solution (Section 2 sparse storage): size and
+    # the time of a compaction and an expansion (synchronous calls)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    off, rows, cols, vals = h.coo_compact(x_dev)
+    t1 = time.perf_counter()
+    back = torch.empty_like(x_dev)
+    h.coo_expand(off, rows, cols, vals, back)
+    t2 = time.perf_counter()
+    nnz = int(rows.numel())
+    coo = {"nnz": nnz, "sparsity": 1.0 - nnz / w.nvox, "bytes": 16 * nnz + 8 * (w.nz + 1),
+           "dense_bytes": 8 * w.nvox, "compact_ms": (t1 - t0) * 1e3, "expand_ms": (t2 - t1) * 1e3,
+           "round_trip_exact": bool(torch.equal(back, x_dev))}
+    del back, rows, cols, vals
+
     ttt = None
     if not args.no_warmstart:
         ttt = time_to_tolerance()
@@ -414,6 +429,7 @@ def main():
                      "tv_launch_kinds": kinds},
         "stages_ms_per_step": {k: stages[k][0] / args.steps for k in main_stages},
         "time_to_tolerance": ttt,
+        "coo": coo,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

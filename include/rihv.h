@@ -187,6 +187,34 @@ rihv_status rihv_batch_destroy(rihv_batch b);
  * scratch contents (x, y, v) are overwritten. */
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_null);
 
+/* Per-plane COO form of a volume (Section 2, GPU implementation paragraph:
+ * volumes stored in the coordinate sparse format, every plane indexing its
+ * own non-zero elements). An element is non-zero unless both its real and
+ * imaginary parts are zero. Plane k's entries occupy [plane_offsets[k],
+ * plane_offsets[k+1]) in row-major order (row j, then column i). rows and cols
+ * are int32 and vals complex64: 16 bytes per entry (the paper counts 8-byte
+ * indices, 24 bytes; int32 covers every supported plane size).
+ *
+ * rihv_coo_compact: x is device complex64 [nz][ny][nx] of the handle's shape,
+ * or NULL for the last solve's result. plane_offsets: device int64 [nz+1],
+ * always written. rows, cols, vals: device arrays of `capacity` entries (16-
+ * byte aligned); *nnz (host) receives the number of non-zeros in every case.
+ * With capacity < *nnz (e.g. 0 and NULL arrays, to query the size) no entry
+ * is written and RIHV_ERR_INVALID_ARG is returned. Deterministic; synchronous
+ * (it reads the count back). */
+rihv_status rihv_coo_compact(rihv_handle h, const void* x_or_null, long long* plane_offsets,
+                             int* rows, int* cols, void* vals, long long capacity,
+                             long long* nnz);
+
+/* Dense x_out (device complex64 [nz][ny][nx]) from a per-plane COO form with
+ * nnz entries: zero everywhere except the listed elements. plane_offsets
+ * (device int64 [nz+1]) are checked on the host before any work (0 first, nnz
+ * last, non-decreasing, at most nx*ny per plane; else RIHV_ERR_INVALID_ARG). An
+ * entry outside its plane is skipped and reported as RIHV_ERR_INVALID_ARG when
+ * the call returns. Synchronous. */
+rihv_status rihv_coo_expand(rihv_handle h, const long long* plane_offsets, const int* rows,
+                            const int* cols, const void* vals, long long nnz, void* x_out);
+
 /* Fused-lasso prox without any allocation. The paper has no counterpart to
  * this entry point; it exists for callers that cannot call cudaMalloc, such
  * as code running while a CUDA graph is captured, hosts that hand out device

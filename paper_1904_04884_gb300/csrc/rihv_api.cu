@@ -101,6 +101,9 @@ struct rihv_ctx {
   double* trace = nullptr;     // device objective trace
   int trace_cap = 0;
   int* det_err = nullptr;
+  int* coo_counts = nullptr;         // per-plane segment counts (COO compaction)
+  long long* coo_seg_off = nullptr;  // their exclusive offsets
+  int* coo_bad = nullptr;            // set by the COO scatter for an entry off the plane
   int* tv_err = nullptr;       // set by a TV kernel whose bounded wait gave up
   CUtensorMap tm_pa[3][3], tm_pb[3][3];   // [one-step, two-step, fused-finalize box]
   DetectWork det{};
@@ -562,6 +565,9 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   AL(h->fin_partials, h->fin_ctas);
   AL(h->red.tickets, 8);
   AL(h->det_err, 1);
+  AL(h->coo_counts, static_cast<size_t>(nz) * coo_segments(nx, ny));
+  AL(h->coo_seg_off, static_cast<size_t>(nz) * coo_segments(nx, ny));
+  AL(h->coo_bad, 1);
   AL(h->tv_err, 1);
 #undef AL
   if (cudaMemset(h->red.tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
@@ -738,6 +744,67 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
   CK(cudaStreamSynchronize(h->stream));
   if (iters_done) *iters_done = done;
   return read_solve_errors(h);
+}
+
+rihv_status rihv_coo_compact(rihv_handle h, const void* x, long long* plane_offsets, int* rows,
+                             int* cols, void* vals, long long capacity, long long* nnz) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (!x) x = h->x;   // the last solve's result
+  CKS(check_dev(h, x, "x"));
+  if (!plane_offsets || !nnz || capacity < 0 || (capacity > 0 && (!rows || !cols || !vals)))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid COO arguments");
+  CKS(check_dev(h, plane_offsets, "plane_offsets"));
+  const float2* xv = static_cast<const float2*>(x);
+  CK(launch_coo_count(xv, h->nx, h->ny, h->nz, h->coo_counts, h->coo_seg_off, plane_offsets,
+                      h->stream));
+  long long total = 0;
+  CK(cudaMemcpyAsync(&total, plane_offsets + h->nz, sizeof(long long), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *nnz = total;
+  if (total > capacity)
+    return fail(h, RIHV_ERR_INVALID_ARG, "COO capacity %lld < %lld non-zeros", capacity, total);
+  if (total > 0) {
+    CKS(check_dev(h, rows, "rows"));
+    CKS(check_dev(h, cols, "cols"));
+    CKS(check_dev(h, vals, "vals"));
+    CK(launch_coo_write(xv, h->nx, h->ny, h->nz, h->coo_seg_off, rows, cols,
+                        static_cast<float2*>(vals), h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return RIHV_OK;
+}
+
+rihv_status rihv_coo_expand(rihv_handle h, const long long* plane_offsets, const int* rows,
+                            const int* cols, const void* vals, long long nnz, void* x_out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (!plane_offsets || !x_out || nnz < 0 || (nnz > 0 && (!rows || !cols || !vals)))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid COO arguments");
+  CKS(check_dev(h, plane_offsets, "plane_offsets"));
+  CKS(check_dev(h, x_out, "x_out"));
+  // offsets are checked on the host before any entry is touched
+  std::vector<long long> off(static_cast<size_t>(h->nz) + 1);
+  CK(cudaMemcpyAsync(off.data(), plane_offsets, off.size() * sizeof(long long),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (off[0] != 0 || off[h->nz] != nnz)
+    return fail(h, RIHV_ERR_INVALID_ARG, "plane offsets must run from 0 to nnz");
+  for (int k = 0; k < h->nz; ++k)
+    if (off[k + 1] < off[k] || off[k + 1] - off[k] > static_cast<long long>(h->nxy))
+      return fail(h, RIHV_ERR_INVALID_ARG, "plane offsets must be non-decreasing, <= nx*ny per plane");
+  if (nnz > 0) {
+    CKS(check_dev(h, rows, "rows"));
+    CKS(check_dev(h, cols, "cols"));
+    CKS(check_dev(h, vals, "vals"));
+  }
+  CK(cudaMemsetAsync(h->coo_bad, 0, sizeof(int), h->stream));
+  CK(launch_coo_scatter(rows, cols, static_cast<const float2*>(vals), plane_offsets, h->nx, h->ny,
+                        h->nz, static_cast<float2*>(x_out), h->coo_bad, h->stream));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->coo_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (bad) return fail(h, RIHV_ERR_INVALID_ARG, "COO entry outside the plane (skipped)");
+  return RIHV_OK;
 }
 
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,

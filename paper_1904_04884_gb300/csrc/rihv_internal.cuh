@@ -230,4 +230,19 @@ void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t*
 cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s);
 size_t conv_smem_bytes(int ck, int n);
 
+// ---------------------------------------------------------------------------
+// Per-plane COO compaction (coo_kernels.cu)
+// ---------------------------------------------------------------------------
+constexpr int kCooSeg = 1024;   // voxels per counting / writing CTA
+int coo_segments(int nx, int ny);
+// counts [nz * segments] int, seg_off [nz * segments], plane_off [nz + 1] (int64)
+cudaError_t launch_coo_count(const float2* x, int nx, int ny, int nz, int* counts, long long* seg_off,
+                             long long* plane_off, cudaStream_t s);
+cudaError_t launch_coo_write(const float2* x, int nx, int ny, int nz, const long long* seg_off,
+                             int* rows, int* cols, float2* vals, cudaStream_t s);
+// zero-fills x, then scatters; *bad = 1 if an entry lies outside the plane
+cudaError_t launch_coo_scatter(const int* rows, const int* cols, const float2* vals,
+                               const long long* plane_off, int nx, int ny, int nz, float2* x,
+                               int* bad, cudaStream_t s);
+
 }  // namespace rihv

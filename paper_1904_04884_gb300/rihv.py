@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "rihv_batch_destroy": (i, [H]),
         "rihv_autotune": (i, [H, ctypes.c_char_p, ctypes.POINTER(i)]),
+        "rihv_coo_compact": (i, [H, vp, vp, vp, vp, vp, ctypes.c_longlong,
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+        "rihv_coo_expand": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -117,7 +120,8 @@ def _ptr(buf, *, device=None, dtype=None, numel=None, name="buffer"):
         raise ValueError(f"{name} must be a CUDA tensor")
     if dtype is not None:
         want = {"complex64": "torch.complex64", "float32": "torch.float32",
-                "float64": "torch.float64"}[np.dtype(dtype).name]
+                "float64": "torch.float64", "int32": "torch.int32",
+                "int64": "torch.int64"}[np.dtype(dtype).name]
         if str(buf.dtype) != want:
             raise ValueError(f"{name} must be {want}, got {buf.dtype}")
     if numel is not None and buf.numel() != numel:
@@ -219,6 +223,43 @@ class Rihv:
             out.append(dict(centroid=(p.cx, p.cy, p.cz), nvox=p.nvox, weight=p.weight,
                             first=p.first))
         return out
+
+    def rihv_coo_compact(self, x=None):
+        """Per-plane COO form of x (None: the last solve's result) as device
+        tensors (plane_offsets int64 [nz+1], rows int32, cols int32, vals
+        complex64); plane k's entries lie at [offsets[k], offsets[k+1]) in
+        row-major order."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device()) if x is None else x.device
+        off = torch.empty(self.nz + 1, dtype=torch.int64, device=dev)
+        xp = _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x") or None
+        nnz = ctypes.c_longlong()
+        st = self.L.rihv_coo_compact(self.h, xp, off.data_ptr(), None, None, None, 0,
+                                     ctypes.byref(nnz))
+        n = nnz.value
+        if st != 0 and n == 0:
+            self._check(st, self.h)
+        rows = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cols = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        vals = torch.empty(max(n, 1), dtype=torch.complex64, device=dev)
+        if n > 0:
+            self._check(self.L.rihv_coo_compact(self.h, xp, off.data_ptr(), rows.data_ptr(),
+                                                cols.data_ptr(), vals.data_ptr(), n,
+                                                ctypes.byref(nnz)), self.h)
+        return off, rows[:n], cols[:n], vals[:n]
+
+    def rihv_coo_expand(self, offsets, rows, cols, vals, x_out):
+        """Dense volume x_out from a per-plane COO form (zeros elsewhere)."""
+        n = int(rows.numel())
+        self._check(self.L.rihv_coo_expand(
+            self.h, _ptr(offsets, device=True, dtype="int64", numel=self.nz + 1, name="offsets"),
+            _ptr(rows, device=True, dtype="int32", name="rows") if n else None,
+            _ptr(cols, device=True, dtype="int32", name="cols") if n else None,
+            _ptr(vals, device=True, dtype="complex64", name="vals") if n else None, n,
+            _ptr(x_out, device=True, dtype="complex64", numel=self.nvox, name="x_out")), self.h)
+
+    coo_compact = rihv_coo_compact
+    coo_expand = rihv_coo_expand
 
     def rihv_autotune(self, cache_path=None):
         """Times the TV z-chunk / steps per launch and the column-pass z-groups on
