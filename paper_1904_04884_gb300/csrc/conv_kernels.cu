@@ -4,19 +4,19 @@
 // Activations are channels-last, [voxel][channel] in BF16, voxel = (z*H + y)*W + x.
 // Weights are W[c_out][tap][c_in], tap = (dz+1)*9 + (dy+1)*3 + (dx+1).
 //
-// Forward and input gradient (implicit GEMM, one CTA per 128 output voxels):
+// Forward and input gradient (implicit GEMM over a halo tile):
 //   D[m][n] = sum_tap sum_k A_tap[m][k] B_tap[n][k]
 //   forward : A = X[v_m + off_tap][k],  B = W[n][tap][k]            (n = c_out)
 //   dgrad   : A = dY[v_m + off_tap][k], B = W[k][26 - tap][n]       (n = c_in)
-// Each tap is one K stage of C_k channels. The stage's A (gathered by the 128
-// threads, one output voxel each, zero outside the volume) and B tiles are
-// written to shared memory in the canonical K-major no-swizzle layout (8x16-byte
-// core matrices; LBO = 128 B along K, SBO = C_k*16 B along M/N), double
-// buffered; one thread issues C_k/16 tcgen05.mma (M = 128, N = C_out, K = 16)
-// into the TMEM accumulator and commits to the stage's mbarrier, which frees
-// the buffer two stages later. The epilogue reads TMEM with tcgen05.ld (warp w
-// owns lanes 32w..32w+31 = its 32 voxels), adds the bias, applies ReLU and
-// stores BF16 or FP32.
+// A CTA owns 128 x 2 output voxels (x, y) of one plane. Per 16 input
+// channels, TMA brings the 3 x 4 x 130 halo of the tile into shared memory in
+// the canonical K-major no-swizzle layout (8 x 16-byte core matrices), so the
+// A operand of every tap is a descriptor offset into the same halo; weights
+// are staged 9 taps at a time, double buffered; one thread issues the
+// tcgen05.mma (M = 128, N = c_out, K = 16) into two TMEM accumulators and
+// commits each stage to an mbarrier. The epilogue reads TMEM with tcgen05.ld
+// (warp w owns lanes 32w..32w+31), adds the bias, applies ReLU and stores
+// BF16 or FP32.
 //
 // Weight gradient (K = voxels, split over CTAs):
 //   D[m][n] = sum_v A[m][v] B[n][v],  m = tap*C_in + c,  n = c_out
@@ -139,27 +139,50 @@ __device__ __forceinline__ void tap_offset(int t, int& dz, int& dy, int& dx) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward / input-gradient kernel
+// Forward / input-gradient kernel (halo tiles by TMA)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// One CTA: a 128 (x) x kTH (y) tile of output voxels in one z plane; kTH
+// accumulators of M = 128 rows. The input (16 channels at a time) arrives as
+// one TMA box per 8-channel group, [dz][dy][x][8 channels] over the tile's
+// 3 x (kTH+2) x 130 halo, zero outside the volume (the convolution's zero
+// padding). In that layout the A operand of tap (dz, dy, dx) for output row
+// mt is already a K-major operand: rows (voxels) 16 bytes apart inside a core
+// matrix, SBO = 128 B between groups of 8 voxels, LBO = one channel group's
+// box between the two K halves. So every tap is only a descriptor start
+// address, and all 27 taps x kTH rows of MMAs run on one staged halo. The
+// weights of 9 taps (one dz plane) are staged per stage in the canonical
+// layout, double buffered; one thread issues the MMAs and commits each stage.
 template <bool DGRAD>
-__global__ void __launch_bounds__(kThreads) k_conv_igemm(const __grid_constant__ ConvArgs a) {
+__global__ void __launch_bounds__(kThreads) k_conv_tile(const __grid_constant__ ConvArgs a,
+                                                         const __grid_constant__ ConvMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ck = a.ck;                  // channels of the gathered input (K per tap)
   const int n = a.n;                    // output channels (MMA N)
-  const int ku = ck / 8;                // 16-byte K units per row
-  const uint32_t a_bytes = kM * ck * 2;
-  const uint32_t b_bytes = n * ck * 2;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
-  unsigned char* stage0 = smem + 128;
-  unsigned char* sa[2] = {stage0, stage0 + a_bytes + b_bytes};
-  unsigned char* sb[2] = {stage0 + a_bytes, stage0 + 2 * a_bytes + b_bytes};
+  const int nchunk = ck / 16;
+  const uint32_t wstage_bytes = 9u * n * 32u;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);   // halo, w0, w1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 32);
+  unsigned char* halo = smem + 128;
+  unsigned char* wbuf[2] = {halo + kConvHaloBytes, halo + kConvHaloBytes + wstage_bytes};
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tmem_cols(n);
+  const uint32_t ncols = tmem_cols(kConvTH * n);
+  const int x0 = blockIdx.x * kConvTW, y0 = blockIdx.y * kConvTH, z = blockIdx.z;
 
   if (tid == 0) {
-    mbar_init(saddr(&bars[0]), 1);
-    mbar_init(saddr(&bars[1]), 1);
+    for (int i = 0; i < 3; ++i) mbar_init(saddr(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(saddr(tmem_slot), ncols);
@@ -167,106 +190,125 @@ __global__ void __launch_bounds__(kThreads) k_conv_igemm(const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
-  const size_t v = static_cast<size_t>(blockIdx.x) * kM + tid;
-  const bool vvalid = v < nvox;
-  const int x = static_cast<int>(v % a.w);
-  const int y = static_cast<int>((v / a.w) % a.h);
-  const int z = static_cast<int>(v / (static_cast<size_t>(a.w) * a.h));
-  const int g = tid >> 3, r = tid & 7;
   const uint32_t idesc = mma_idesc(kM, n, 0, 0);
-  const uint32_t sbo = ku * 128;
+  const uint32_t halo_a = saddr(halo);
   bool ok = true;
-  int issued = -1;
+  int stage = 0, last_commit = -1;
+  int halo_pending = -1;   // chunk whose halo load may still be in flight
 
-  for (int t = 0; t < 27 && ok; ++t) {
-    const int buf = t & 1;
-    if (t >= 2) {
-      const bool w_ok = mbar_wait(saddr(&bars[buf]), ((t - 2) >> 1) & 1);
+  for (int c = 0; c < nchunk && ok; ++c) {
+    // the previous chunk's MMAs read the halo: wait for its last commit
+    if (last_commit >= 0) {
+      const bool w_ok = mbar_wait(saddr(&bars[1 + (last_commit & 1)]), (last_commit >> 1) & 1);
       ok = __syncthreads_and(w_ok) != 0;
       if (!ok) break;
     }
-    int dz, dy, dx;
-    tap_offset(t, dz, dy, dx);
-    // A: this thread's voxel row
-    {
-      const int zz = z + dz, yy = y + dy, xx = x + dx;
-      const bool inb = vvalid && zz >= 0 && zz < a.d && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-      const uint4* src = reinterpret_cast<const uint4*>(
-          a.x + (inb ? ((static_cast<size_t>(zz) * a.h + yy) * a.w + xx) * ck : 0));
-      unsigned char* dst = sa[buf] + g * ku * 128 + r * 16;
-      for (int k = 0; k < ku; ++k) {
-        const uint4 val = inb ? __ldg(src + k) : make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(dst + k * 128) = val;
-      }
-    }
-    // B: weights of this tap
-    for (int u = tid; u < n * ku; u += kThreads) {
-      const int nn = u / ku, k = u - nn * ku;
-      uint4 val;
-      if (!DGRAD) {
-        val = __ldg(reinterpret_cast<const uint4*>(a.w_ + (static_cast<size_t>(nn) * 27 + t) * ck) + k);
-      } else {
-        // W is [ck = c_out][27][n = c_in]; B[nn][kk] = W[kk][26 - t][nn]
-        uint16_t e[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int kk = k * 8 + j;
-          e[j] = reinterpret_cast<const uint16_t*>(a.w_)[(static_cast<size_t>(kk) * 27 + (26 - t)) * n + nn];
-        }
-        val = make_uint4(e[0] | (static_cast<uint32_t>(e[1]) << 16), e[2] | (static_cast<uint32_t>(e[3]) << 16),
-                         e[4] | (static_cast<uint32_t>(e[5]) << 16), e[6] | (static_cast<uint32_t>(e[7]) << 16));
-      }
-      *reinterpret_cast<uint4*>(sb[buf] + ((nn >> 3) * ku + k) * 128 + (nn & 7) * 16) = val;
-    }
-    fence_async_smem();
-    __syncthreads();
     if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = saddr(sa[buf]), b0 = saddr(sb[buf]);
-      for (int s = 0; s < ck / 16; ++s)
-        umma_bf16(tmem, smem_desc(a0 + s * 256, 128, sbo), smem_desc(b0 + s * 256, 128, sbo), idesc,
-                  (t > 0 || s > 0) ? 1u : 0u);
-      umma_commit(saddr(&bars[buf]));
+      mbar_expect_tx(saddr(&bars[0]), kConvHaloBytes);
+      for (int j = 0; j < 2; ++j)
+        tma_load_4d(halo_a + j * kConvHaloKu, &maps.m[2 * c + j], 0, x0 - 1, y0 - 1, z - 1,
+                    saddr(&bars[0]));
     }
-    issued = t;
+    halo_pending = c;
+    for (int dz = 0; dz < 3 && ok; ++dz, ++stage) {
+      const int buf = stage & 1;
+      if (stage >= 2) {
+        const bool w_ok = mbar_wait(saddr(&bars[1 + buf]), ((stage - 2) >> 1) & 1);
+        ok = __syncthreads_and(w_ok) != 0;
+        if (!ok) break;
+      }
+      // weights of taps dz*9 .. dz*9+8, channels 16c .. 16c+15:
+      // [tap][n/8][2 K halves][8 rows][16 B]
+      for (int u = tid; u < 9 * n * 2; u += kThreads) {
+        const int tl = u / (2 * n), rem = u - tl * 2 * n, nn = rem >> 1, j = rem & 1;
+        const int t = dz * 9 + tl;
+        uint4 val;
+        if (!DGRAD) {
+          val = __ldg(reinterpret_cast<const uint4*>(a.w_ + (static_cast<size_t>(nn) * 27 + t) * ck) +
+                      2 * c + j);
+        } else {
+          // W is [ck = c_out][27][n = c_in]; B[nn][kk] = W[kk][26 - t][nn]
+          uint16_t e[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int kk = (2 * c + j) * 8 + q;
+            e[q] = reinterpret_cast<const uint16_t*>(a.w_)[(static_cast<size_t>(kk) * 27 + (26 - t)) * n + nn];
+          }
+          val = make_uint4(e[0] | (static_cast<uint32_t>(e[1]) << 16), e[2] | (static_cast<uint32_t>(e[3]) << 16),
+                           e[4] | (static_cast<uint32_t>(e[5]) << 16), e[6] | (static_cast<uint32_t>(e[7]) << 16));
+        }
+        *reinterpret_cast<uint4*>(wbuf[buf] + tl * n * 32 + ((nn >> 3) * 2 + j) * 128 + (nn & 7) * 16) = val;
+      }
+      fence_async_smem();
+      if (dz == 0) {
+        const bool w_ok = mbar_wait(saddr(&bars[0]), c & 1);
+        ok = __syncthreads_and(w_ok) != 0;
+        if (!ok) break;
+        halo_pending = -1;
+      } else {
+        __syncthreads();
+      }
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t b0 = saddr(wbuf[buf]);
+        for (int tl = 0; tl < 9; ++tl) {
+          const int dy = tl / 3, dx = tl - (tl / 3) * 3;
+          const uint64_t bdesc = smem_desc(b0 + tl * n * 32, 128, 256);
+#pragma unroll
+          for (int mt = 0; mt < kConvTH; ++mt) {
+            const uint32_t aoff = ((dz * (kConvTH + 2) + mt + dy) * kConvHX + dx) * 16;
+            umma_bf16(tmem + mt * n, smem_desc(halo_a + aoff, kConvHaloKu, 128), bdesc, idesc,
+                      (c > 0 || dz > 0 || tl > 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(saddr(&bars[1 + buf]));
+      }
+      last_commit = stage;
+    }
   }
 
-  // all MMAs done: the commit after the last issued stage
-  if (issued >= 0) {
-    const bool w_ok = mbar_wait(saddr(&bars[issued & 1]), (issued >> 1) & 1);
+  // all MMAs done: the commit after the last stage
+  if (last_commit >= 0) {
+    const bool w_ok = mbar_wait(saddr(&bars[1 + (last_commit & 1)]), (last_commit >> 1) & 1);
     ok = (__syncthreads_and(w_ok) != 0) && ok;
   }
   if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      if (halo_pending >= 0) mbar_wait(saddr(&bars[0]), halo_pending & 1);   // drain (bounded)
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, ncols);
     return;
   }
   tc_fence_after();
-  // epilogue: warp w reads TMEM lanes 32w..32w+31 (its voxels)
-  const size_t vo = static_cast<size_t>(blockIdx.x) * kM + warp * 32 + lane;
-  for (int c0 = 0; c0 < n; c0 += 8) {
-    float acc[8];
-    tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, acc);
-    if (vo < nvox) {
+  // epilogue: warp w reads TMEM lanes 32w..32w+31 (voxels x0 + tid) of every row
+  const int x = x0 + warp * 32 + lane;
+  for (int mt = 0; mt < kConvTH; ++mt) {
+    const int y = y0 + mt;
+    const bool valid = x < a.w && y < a.h;
+    const size_t vo = (static_cast<size_t>(z) * a.h + y) * a.w + x;
+    for (int c0 = 0; c0 < n; c0 += 8) {
+      float acc[8];
+      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + mt * n + c0, acc);
+      if (valid) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (a.bias) acc[j] += a.bias[c0 + j];
-        if (a.relu) acc[j] = fmaxf(acc[j], 0.f);
-      }
-      if (a.out_f32) {
-        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vo * n + c0);
-        dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-      } else {
-        __nv_bfloat162 p[4];
+        for (int j = 0; j < 8; ++j) {
+          if (a.bias) acc[j] += a.bias[c0 + j];
+          if (a.relu) acc[j] = fmaxf(acc[j], 0.f);
+        }
+        if (a.out_f32) {
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vo * n + c0);
+          dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+          dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+          __nv_bfloat162 p[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
-        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vo * n + c0) =
-            *reinterpret_cast<uint4*>(p);
+          for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(acc[2 * j], acc[2 * j + 1]);
+          *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vo * n + c0) =
+              *reinterpret_cast<uint4*>(p);
+        }
       }
     }
   }
@@ -406,18 +448,35 @@ __global__ void k_wgrad_reduce(const float* partial, int nsplit, int mpad, int c
 
 }  // namespace
 
-size_t conv_smem_bytes(int ck, int n) { return 128 + 2 * (static_cast<size_t>(kM) * ck * 2 + n * ck * 2); }
+size_t conv_smem_bytes(int ck, int n) {
+  (void)ck;
+  return 128 + kConvHaloBytes + 2 * 9 * static_cast<size_t>(n) * 32;
+}
 size_t wgrad_smem_bytes(int cout) { return 128 + 2 * (static_cast<size_t>(kM) * kWgK * 2 + cout * kWgK * 2); }
 
 cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s) {
-  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
-  const unsigned grid = static_cast<unsigned>((nvox + kM - 1) / kM);
+  // one 4D tensor map per 8-channel group of the gathered input:
+  // dims (8 channels, x, y, z), box (8, 130, kTH + 2, 3), zero fill
+  ConvMaps maps;
+  const int groups = a.ck / 8;
+  if (groups > kConvMaxGroups || a.ck % 16 != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(a.w), static_cast<cuuint64_t>(a.h),
+                              static_cast<cuuint64_t>(a.d)};
+  const cuuint64_t row = static_cast<cuuint64_t>(a.ck) * 2;
+  const cuuint64_t strides[3] = {row, row * a.w, row * a.w * a.h};
+  const cuuint32_t box[4] = {8, kConvHX, kConvTH + 2, 3};
+  for (int g = 0; g < groups; ++g) {
+    cudaError_t e = encode_tmap(&maps.m[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, a.x + g * 8, dims,
+                                strides, box);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((a.w + kConvTW - 1) / kConvTW, (a.h + kConvTH - 1) / kConvTH, a.d);
   const size_t smem = conv_smem_bytes(a.ck, a.n);
-  auto kern = dgrad ? k_conv_igemm<true> : k_conv_igemm<false>;
+  auto kern = dgrad ? k_conv_tile<true> : k_conv_tile<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, s>>>(a);
+  kern<<<grid, kThreads, smem, s>>>(a, maps);
   return cudaGetLastError();
 }
 

@@ -225,7 +225,21 @@ struct WgradArgs {
   size_t vox_per_split;
   int* err;
 };
+// Halo-tile geometry of the forward / input-gradient convolution.
+constexpr int kConvTW = 128;                   // output voxels along x per CTA (MMA M)
+constexpr int kConvTH = 2;                     // output rows (y) per CTA
+constexpr int kConvHX = kConvTW + 2;           // halo width
+constexpr int kConvHaloKu = 3 * (kConvTH + 2) * kConvHX * 16;   // bytes per 8-channel group
+constexpr int kConvHaloBytes = 2 * kConvHaloKu;                 // 16 channels
+constexpr int kConvMaxGroups = 32;             // 256 channels / 8
+struct ConvMaps {
+  CUtensorMap m[kConvMaxGroups];
+};
 cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s);
+// Tiled tensor map (no interleave, no swizzle, 256-byte L2 promotion, zero
+// fill out of bounds); rank <= 5, strides in bytes for dims 1..rank-1.
+cudaError_t encode_tmap(CUtensorMap* tm, CUtensorMapDataType type, int rank, const void* base,
+                        const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box);
 void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t* vps);
 cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s);
 size_t conv_smem_bytes(int ck, int n);

@@ -917,10 +917,8 @@ int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
   return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
 }
 
-// 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box
-// of box_rows rows x 2 box_cols floats x 1 plane, zero fill out of bounds.
-cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
-                             int box_rows, int box_cols) {
+cudaError_t encode_tmap(CUtensorMap* tm, CUtensorMapDataType type, int rank, const void* base,
+                        const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -934,16 +932,23 @@ cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, 
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<EncodeFn>(fn);
   }
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = encode(tm, type, static_cast<cuuint32_t>(rank), const_cast<void*>(base), dims, strides,
+                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 3D tensor map over a complex64 volume viewed as float32 [nz][ny][2 nx], box
+// of box_rows rows x 2 box_cols floats x 1 plane, zero fill out of bounds.
+cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
+                             int box_rows, int box_cols) {
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(2 * nx), static_cast<cuuint64_t>(ny),
                               static_cast<cuuint64_t>(nz)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(8) * nx,
                                  static_cast<cuuint64_t>(8) * nx * ny};
   const cuuint32_t box[3] = {static_cast<cuuint32_t>(2 * box_cols), static_cast<cuuint32_t>(box_rows), 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
-                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  return encode_tmap(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box);
 }
 
 cudaError_t launch_finalize(int mode, const FinArgs& a, cudaStream_t s) {

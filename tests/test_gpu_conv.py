@@ -25,7 +25,7 @@ def _rel(a, b):
 
 
 CASES = [((5, 6, 40), 16, 16), ((4, 8, 16), 32, 64), ((3, 4, 32), 96, 32), ((2, 3, 7), 48, 16),
-         ((6, 6, 6), 16, 32)]
+         ((6, 6, 6), 16, 32), ((2, 5, 200), 32, 16), ((3, 9, 130), 16, 64)]
 
 
 @pytest.mark.parametrize("dims,cin,cout", CASES)
