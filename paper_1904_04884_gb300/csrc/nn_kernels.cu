@@ -95,6 +95,144 @@ __global__ void k_upsample2_grad(const uint16_t* gy, uint16_t* gx, int d, int h,
   }
 }
 
+// ---- 8-channel (16-byte) vector forms, used when every channel count is a
+// multiple of 8 and every pointer 16-byte aligned; per channel they add in
+// the same order as the scalar forms above, so the results are identical.
+__device__ __forceinline__ void unpack8(uint4 u, float* f) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float* f) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = static_cast<uint32_t>(to_bf(f[2 * i])) | (static_cast<uint32_t>(to_bf(f[2 * i + 1])) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void k_avgpool2_v8(const uint4* x, uint4* y, int d, int h, int w, int g) {
+  const int od = d / 2, oh = h / 2, ow = w / 2;
+  const size_t total = static_cast<size_t>(od) * oh * ow * g;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int cg = static_cast<int>(i % g);
+    size_t v = i / g;
+    const int ox = static_cast<int>(v % ow); v /= ow;
+    const int oy = static_cast<int>(v % oh);
+    const int oz = static_cast<int>(v / oh);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 8; ++k) {
+      const int zz = 2 * oz + (k >> 2), yy = 2 * oy + ((k >> 1) & 1), xx = 2 * ox + (k & 1);
+      float f[8];
+      unpack8(x[((static_cast<size_t>(zz) * h + yy) * w + xx) * g + cg], f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s[j] += f[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] *= 0.125f;
+    y[i] = pack8(s);
+  }
+}
+
+__global__ void k_avgpool2_grad_v8(const uint4* gy, uint4* gx, int d, int h, int w, int g) {
+  const size_t total = static_cast<size_t>(d) * h * w * g;
+  const int oh = h / 2, ow = w / 2;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int cg = static_cast<int>(i % g);
+    size_t v = i / g;
+    const int x = static_cast<int>(v % w); v /= w;
+    const int y = static_cast<int>(v % h);
+    const int z = static_cast<int>(v / h);
+    float f[8];
+    unpack8(gy[((static_cast<size_t>(z / 2) * oh + y / 2) * ow + x / 2) * g + cg], f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] *= 0.125f;
+    gx[i] = pack8(f);
+  }
+}
+
+__global__ void k_upsample2_v8(const uint4* x, uint4* y, int d, int h, int w, int g) {
+  const int od = 2 * d, oh = 2 * h, ow = 2 * w;
+  const size_t total = static_cast<size_t>(od) * oh * ow * g;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int cg = static_cast<int>(i % g);
+    size_t v = i / g;
+    const int xx = static_cast<int>(v % ow); v /= ow;
+    const int yy = static_cast<int>(v % oh);
+    const int zz = static_cast<int>(v / oh);
+    y[i] = x[((static_cast<size_t>(zz / 2) * h + yy / 2) * w + xx / 2) * g + cg];
+  }
+}
+
+__global__ void k_upsample2_grad_v8(const uint4* gy, uint4* gx, int d, int h, int w, int g) {
+  const size_t total = static_cast<size_t>(d) * h * w * g;
+  const int oh = 2 * h, ow = 2 * w;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int cg = static_cast<int>(i % g);
+    size_t v = i / g;
+    const int x = static_cast<int>(v % w); v /= w;
+    const int y = static_cast<int>(v % h);
+    const int z = static_cast<int>(v / h);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 8; ++k) {
+      const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+      float f[8];
+      unpack8(gy[((static_cast<size_t>(zz) * oh + yy) * ow + xx) * g + cg], f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s[j] += f[j];
+    }
+    gx[i] = pack8(s);
+  }
+}
+
+__global__ void k_concat_v8(const uint4* a, const uint4* b, uint4* out, size_t voxels, int ga, int gb) {
+  const int g = ga + gb;
+  const size_t total = voxels * g;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i / g;
+    const int cg = static_cast<int>(i - v * g);
+    out[i] = cg < ga ? a[v * ga + cg] : b[v * gb + (cg - ga)];
+  }
+}
+
+__global__ void k_split_v8(const uint4* gsrc, uint4* ga_out, uint4* gb_out, size_t voxels, int ga, int gb) {
+  const int g = ga + gb;
+  const size_t total = voxels * g;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i / g;
+    const int cg = static_cast<int>(i - v * g);
+    if (cg < ga)
+      ga_out[v * ga + cg] = gsrc[i];
+    else
+      gb_out[v * gb + (cg - ga)] = gsrc[i];
+  }
+}
+
+__global__ void k_pack_input_v8(const float2* vol, uint4* out, size_t voxels, int g, float scale) {
+  const size_t total = voxels * g;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i / g;
+    const int cg = static_cast<int>(i - v * g);
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (cg == 0) {
+      const float2 c = vol[v];
+      f[0] = scale * c.x;
+      f[1] = scale * c.y;
+    }
+    out[i] = pack8(f);
+  }
+}
+
 __global__ void k_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<size_t>(gridDim.x) * blockDim.x)
@@ -343,7 +481,11 @@ rihv_status rihv_nn_avgpool2(const uint16_t* x, uint16_t* y, int d, int h, int w
                              void* stream) {
   if (!x || !y || d < 2 || h < 2 || wd < 2 || (d | h | wd) & 1 || c < 1) return RIHV_ERR_INVALID_ARG;
   const size_t n = static_cast<size_t>(d / 2) * (h / 2) * (wd / 2) * c;
-  k_avgpool2<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, d, h, wd, c);
+  if (c % 8 == 0 && aligned16(x) && aligned16(y))
+    k_avgpool2_v8<<<grid_for(n / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(x), reinterpret_cast<uint4*>(y), d, h, wd, c / 8);
+  else
+    k_avgpool2<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, d, h, wd, c);
   return launched();
 }
 
@@ -351,7 +493,11 @@ rihv_status rihv_nn_avgpool2_grad(const uint16_t* gy, uint16_t* gx, int d, int h
                                   void* stream) {
   if (!gy || !gx || d < 2 || h < 2 || wd < 2 || (d | h | wd) & 1 || c < 1) return RIHV_ERR_INVALID_ARG;
   const size_t n = static_cast<size_t>(d) * h * wd * c;
-  k_avgpool2_grad<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(gy, gx, d, h, wd, c);
+  if (c % 8 == 0 && aligned16(gy) && aligned16(gx))
+    k_avgpool2_grad_v8<<<grid_for(n / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(gy), reinterpret_cast<uint4*>(gx), d, h, wd, c / 8);
+  else
+    k_avgpool2_grad<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(gy, gx, d, h, wd, c);
   return launched();
 }
 
@@ -359,7 +505,11 @@ rihv_status rihv_nn_upsample2(const uint16_t* x, uint16_t* y, int d, int h, int 
                               void* stream) {
   if (!x || !y || d < 1 || h < 1 || wd < 1 || c < 1) return RIHV_ERR_INVALID_ARG;
   const size_t n = static_cast<size_t>(8) * d * h * wd * c;
-  k_upsample2<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, d, h, wd, c);
+  if (c % 8 == 0 && aligned16(x) && aligned16(y))
+    k_upsample2_v8<<<grid_for(n / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(x), reinterpret_cast<uint4*>(y), d, h, wd, c / 8);
+  else
+    k_upsample2<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, d, h, wd, c);
   return launched();
 }
 
@@ -367,7 +517,11 @@ rihv_status rihv_nn_upsample2_grad(const uint16_t* gy, uint16_t* gx, int d, int 
                                    void* stream) {
   if (!gy || !gx || d < 1 || h < 1 || wd < 1 || c < 1) return RIHV_ERR_INVALID_ARG;
   const size_t n = static_cast<size_t>(d) * h * wd * c;
-  k_upsample2_grad<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(gy, gx, d, h, wd, c);
+  if (c % 8 == 0 && aligned16(gy) && aligned16(gx))
+    k_upsample2_grad_v8<<<grid_for(n / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(gy), reinterpret_cast<uint4*>(gx), d, h, wd, c / 8);
+  else
+    k_upsample2_grad<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(gy, gx, d, h, wd, c);
   return launched();
 }
 
@@ -381,24 +535,38 @@ rihv_status rihv_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, siz
 rihv_status rihv_nn_concat(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t voxels,
                            int ca, int cb, void* stream) {
   if (!a || !b || !out || ca < 1 || cb < 1) return RIHV_ERR_INVALID_ARG;
-  k_concat<<<grid_for(voxels * (ca + cb)), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, out, voxels,
-                                                                                     ca, cb);
+  if (ca % 8 == 0 && cb % 8 == 0 && aligned16(a) && aligned16(b) && aligned16(out))
+    k_concat_v8<<<grid_for(voxels * (ca + cb) / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(a), reinterpret_cast<const uint4*>(b), reinterpret_cast<uint4*>(out),
+        voxels, ca / 8, cb / 8);
+  else
+    k_concat<<<grid_for(voxels * (ca + cb)), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, out, voxels,
+                                                                                       ca, cb);
   return launched();
 }
 
 rihv_status rihv_nn_split(const uint16_t* g, uint16_t* ga, uint16_t* gb, size_t voxels, int ca,
                           int cb, void* stream) {
   if (!g || !ga || !gb || ca < 1 || cb < 1) return RIHV_ERR_INVALID_ARG;
-  k_split<<<grid_for(voxels * (ca + cb)), 256, 0, static_cast<cudaStream_t>(stream)>>>(g, ga, gb, voxels,
-                                                                                    ca, cb);
+  if (ca % 8 == 0 && cb % 8 == 0 && aligned16(g) && aligned16(ga) && aligned16(gb))
+    k_split_v8<<<grid_for(voxels * (ca + cb) / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(g), reinterpret_cast<uint4*>(ga), reinterpret_cast<uint4*>(gb),
+        voxels, ca / 8, cb / 8);
+  else
+    k_split<<<grid_for(voxels * (ca + cb)), 256, 0, static_cast<cudaStream_t>(stream)>>>(g, ga, gb, voxels,
+                                                                                      ca, cb);
   return launched();
 }
 
 rihv_status rihv_nn_pack_input(const void* vol, uint16_t* out, size_t voxels, int c, float scale,
                                void* stream) {
   if (!vol || !out || c < 2) return RIHV_ERR_INVALID_ARG;
-  k_pack_input<<<grid_for(voxels * c), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const float2*>(vol), out, voxels, c, scale);
+  if (c % 8 == 0 && aligned16(out))
+    k_pack_input_v8<<<grid_for(voxels * c / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float2*>(vol), reinterpret_cast<uint4*>(out), voxels, c / 8, scale);
+  else
+    k_pack_input<<<grid_for(voxels * c), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float2*>(vol), out, voxels, c, scale);
   return launched();
 }
 
