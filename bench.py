@@ -58,6 +58,31 @@ def dist_env():
     return rank, world, local
 
 
+def rank_hologram(b, w, rank):
+    """Each rank reconstructs its own frame: rank 0 the workload's hologram,
+    rank r > 0 the same with an added noise draw of its own (seed 1000 + r)."""
+    if rank == 0:
+        return b
+    from paper_1904_04884_gb300 import synth
+    return (b + w.sigma * synth.Stream(1000 + rank).normal(w.nx * w.ny).reshape(b.shape)
+            ).astype(np.float32)
+
+
+def max_over_ranks(pg, values):
+    """Element-wise maximum of host float timings over all ranks (gloo)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64)
+    if pg:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_value(vox_per_step, steps, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank solves its own frame)."""
+    return vox_per_step * steps * world / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -279,7 +304,9 @@ def run_reference(args, rank, world):
         "unit": "voxel-iter/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "sample": sample},
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "iters": w.iters,
+                   "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
+                   "parallelism": f"replicas x{world}", "sample": sample},
         "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0,
@@ -314,12 +341,7 @@ def main():
     h = Rihv(*w.optics_tuple(), stream=stream)
     h.set_options(tv_dims=w.tv_dims, n_inner=w.n_inner, check_every=10)
 
-    b = make_hologram(w, h, torch, dev)
-    # each rank reconstructs its own frame: a different noise draw per rank
-    if rank:
-        from paper_1904_04884_gb300 import synth
-        b = (b + w.sigma * synth.Stream(1000 + rank).normal(w.nx * w.ny).reshape(b.shape)
-             ).astype(np.float32)
+    b = rank_hologram(make_hologram(w, h, torch, dev), w, rank)
     b_dev = torch.from_numpy(b).to(dev)
     x_dev = torch.empty(w.shape, dtype=torch.complex64, device=dev)
     trace = torch.empty(w.iters // 10, dtype=torch.float64, device=dev)
@@ -377,16 +399,13 @@ def main():
         step_host()
     e2e_s = time.perf_counter() - t0
 
-    times = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64)
-    if pg:
-        pg.all_reduce(times, op=pg.ReduceOp.MAX)
-    ms, e2e_ms = float(times[0]), float(times[1])
+    ms, e2e_ms = max_over_ranks(pg, [ms, e2e_s * 1e3])
 
     if rank != 0:
         return
     vox_iters = w.nvox * w.iters
-    value = vox_iters * args.steps * world / (ms / 1e3)
-    e2e_value = vox_iters * e2e_steps * world / (e2e_ms / 1e3)
+    value = job_value(vox_iters, args.steps, world, ms)
+    e2e_value = job_value(vox_iters, e2e_steps, world, e2e_ms)
 
     # Roofline of the dominant kernel, the TV launch that reads p (two dual
     # steps per launch by default), from the per-launch CUDA events the
