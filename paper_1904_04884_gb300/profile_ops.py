@@ -23,8 +23,8 @@ def main():
     p.add_argument("--inner", type=int, default=20)
     p.add_argument("--iters", type=int, default=10)
     p.add_argument("--reps", type=int, default=3)
-    p.add_argument("--tv-per-launch", type=int, default=1, choices=[1, 2],
-                   help="dual TV steps per kernel launch")
+    p.add_argument("--tv-per-launch", type=int, default=2, choices=[1, 2],
+                   help="dual TV steps per kernel launch (library default 2)")
     a = p.parse_args()
 
     import torch
