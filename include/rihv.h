@@ -167,15 +167,25 @@ rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_
  * holograms[i]: host or device float32 hologram of handle i; x0s: NULL or an
  * array of host or device warm-start volumes; x_outs[i]: host or device
  * complex64 output volume; traces: NULL or per-handle host or device arrays
- * of iters / check_every doubles (NULL entries allowed). Fixed iteration
- * count: handles with f_star > 0 are rejected (RIHV_ERR_INVALID_ARG). The call
- * returns after the batch has finished. */
+ * of iters / check_every doubles (NULL entries allowed). Handles whose
+ * options set a stop test stop early inside the graph (see
+ * rihv_batch_iterations); the others run `iters`. The call returns after the
+ * batch has finished. */
 typedef struct rihv_batch_st* rihv_batch;
 rihv_status rihv_batch_create(const rihv_handle* handles, int n, rihv_batch* out);
 rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float lambda_l1,
                              float lambda_tv, int iters, const void* const* x0s_or_null,
                              void* const* x_outs, double* const* traces_or_null);
 rihv_status rihv_batch_destroy(rihv_batch b);
+/* Iterations each hologram of the batch ran in the last rihv_batch_solve
+ * (iters_done: host int[n], in handle order). A handle whose options set a
+ * stop test (f_star > 0, check_every > 0) stops at the first objective check
+ * that meets F(x_k) <= f_star (1 + tol), exactly where rihv_solve stops: the
+ * batch graph then runs its iterations in chunks of check_every, every chunk
+ * after the first behind a conditional (IF) graph node whose condition the
+ * previous chunk sets on the device; objective checks it does not reach read
+ * as NaN in its trace. Without a stop test all holograms run `iters`. */
+rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done);
 
 /* Autotuner (not in the paper). Times, on the handle's own scratch, the TV
  * kernel's z-chunk length (8..256 planes per CTA) and steps per launch (1 or

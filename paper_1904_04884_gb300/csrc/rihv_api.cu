@@ -136,6 +136,9 @@ struct rihv_batch_st {
   std::vector<int> tunes;            // zchunk, zpg per handle
   std::vector<std::vector<long long>> launches;   // per handle, per stage, per graph launch
   std::vector<int> checks;           // objective checks per handle per launch
+  bool conditional = false;          // graph with per-hologram stop tests (IF nodes)
+  int* done_dev = nullptr;           // per handle: iterations run by the last launch
+  std::vector<int> done;             // host copy after the last launch
 };
 
 namespace {
@@ -438,6 +441,24 @@ rihv_status ensure_trace(rihv_ctx* h, int nchecks) {
 
 // Solve set-up from the hologram already in h->holo: F b, x_0 (zero unless
 // warm, in which case h->x already holds it), y_1 = x_0, scalars, flags.
+// End of a chunk of FISTA iterations inside a batched graph: records the
+// iterations run and, if a chunk follows, sets its IF condition: stop once
+// the objective just computed is <= the threshold (rihv_solve's test).
+__global__ void k_chunk_end(int* done, int k_end, const double* f, double thr,
+                            cudaGraphConditionalHandle next, int has_next) {
+  *done = k_end;
+  if (has_next) {
+    const double v = *f;
+    cudaGraphSetConditional(next, (v <= thr) ? 0u : 1u);
+  }
+}
+
+cudaError_t launch_chunk_end(int* done, int k_end, const double* f, double thr,
+                             cudaGraphConditionalHandle next, int has_next, cudaStream_t s) {
+  k_chunk_end<<<1, 1, 0, s>>>(done, k_end, f, thr, next, has_next && f ? 1 : 0);
+  return cudaGetLastError();
+}
+
 rihv_status enqueue_setup(rihv_ctx* h, bool warm) {
   StageScope sc(h, ST_SETUP, 3);
   CKS(fft2_plane(h, h->holo, true, h->bhat));
@@ -931,9 +952,11 @@ rihv_status rihv_batch_create(const rihv_handle* hs, int n, rihv_batch* out) {
   for (int i = 0; ok && i < n; ++i)
     ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->done_dev, sizeof(int) * n) == cudaSuccess;
+  b->done.assign(n, 0);
   if (!ok) {
     rihv_batch_destroy(b);
-    return fail(nullptr, RIHV_ERR_CUDA, "stream or event creation failed");
+    return fail(nullptr, RIHV_ERR_CUDA, "stream, event or counter allocation failed");
   }
   *out = b;
   return RIHV_OK;
@@ -949,6 +972,7 @@ rihv_status rihv_batch_destroy(rihv_batch b) {
     if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->master) cudaStreamDestroy(b->master);
+  if (b->done_dev) cudaFree(b->done_dev);
   delete b;
   return RIHV_OK;
 }
@@ -956,7 +980,141 @@ rihv_status rihv_batch_destroy(rihv_batch b) {
 static bool same_options(const rihv_options& a, const rihv_options& o) {
   return a.tv_dims == o.tv_dims && a.restart == o.restart && a.accelerate == o.accelerate &&
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
-         a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize;
+         a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
+         a.f_star == o.f_star && a.tol == o.tol;
+}
+
+// Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a
+// standalone graph.
+static rihv_status capture_graph(rihv_ctx* h, cudaStream_t st, cudaGraph_t* g,
+                                 const std::function<rihv_status()>& fn) {
+  cudaStream_t saved = h->stream;
+  const int saved_prof = h->prof;
+  h->stream = st;
+  h->prof = 0;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    h->stream = saved;
+    h->prof = saved_prof;
+    return fail(h, RIHV_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  }
+  rihv_status r = fn();
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(st, &graph);
+  h->stream = saved;
+  h->prof = saved_prof;
+  if (r != RIHV_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e != cudaSuccess) return fail(h, RIHV_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  *g = graph;
+  return RIHV_OK;
+}
+
+// Batched graph with a stop test per hologram (handles with f_star > 0):
+// setup, then the iterations in chunks of check_every, each chunk after the
+// first inside an IF node whose condition the previous chunk's last kernel
+// sets from its objective (stop once F(x_k) <= f_star (1 + tol)). So every
+// hologram stops at the first check that meets its
+// tolerance, exactly where rihv_solve would, while the batch shares one graph.
+// Handles without a stop test run all iterations in one child graph.
+static rihv_status batch_capture_cond(rihv_batch b, float l1, float ltv, int iters, bool warm) {
+  const int n = static_cast<int>(b->hs.size());
+  rihv_ctx* h0 = b->hs[0];
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->launches.assign(n, std::vector<long long>(kNumStages, 0));
+  b->checks.assign(n, 0);
+  cudaGraph_t root = nullptr;
+  if (cudaGraphCreate(&root, 0) != cudaSuccess) return fail(h0, RIHV_ERR_CUDA, "graph create");
+  std::vector<cudaGraph_t> parts;   // standalone graphs, destroyed after cloning
+  auto add_child = [&](cudaGraph_t into, cudaGraph_t g, const cudaGraphNode_t* dep,
+                       cudaGraphNode_t* node) {
+    parts.push_back(g);
+    return cudaGraphAddChildGraphNode(node, into, dep, dep ? 1 : 0, g);
+  };
+  rihv_status st = RIHV_OK;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && st == RIHV_OK && e == cudaSuccess; ++i) {
+    rihv_ctx* h = b->hs[i];
+    const int M = h->opt.check_every;
+    const bool stop = h->opt.f_star > 0.0 && M > 0;
+    const double thr = h->opt.f_star * (1.0 + h->opt.tol);
+    long long before[kNumStages];
+    for (int s = 0; s < kNumStages; ++s) before[s] = h->stage_launches[s];
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t prev = nullptr, node = nullptr;
+    int check = 0;
+    st = capture_graph(h, b->branch[i], &g, [&] { return enqueue_setup(h, warm); });
+    if (st != RIHV_OK) break;
+    e = add_child(root, g, nullptr, &node);
+    prev = node;
+    const int chunk = stop ? M : iters;
+    cudaGraphConditionalHandle next = 0;
+    for (int k0 = 1; k0 <= iters && st == RIHV_OK && e == cudaSuccess; k0 += chunk) {
+      const int k1 = std::min(iters, k0 + chunk - 1);
+      const bool has_next = stop && k1 < iters && k1 % M == 0;
+      cudaGraphConditionalHandle mine = next;
+      next = 0;
+      if (has_next) {
+        e = cudaGraphConditionalHandleCreate(&next, root, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+      }
+      const double* fk = nullptr;
+      st = capture_graph(h, b->branch[i], &g, [&]() -> rihv_status {
+        for (int k = k0; k <= k1; ++k) CKS(enqueue_iteration(h, k, l1, ltv, &check));
+        fk = (M > 0 && k1 % M == 0 && check > 0) ? h->trace + (check - 1) : nullptr;
+        CK(launch_chunk_end(b->done_dev + i, k1, fk, thr, next, has_next ? 1 : 0, h->stream));
+        return RIHV_OK;
+      });
+      if (st != RIHV_OK) break;
+      if (k0 == 1) {
+        e = add_child(root, g, &prev, &node);
+      } else {
+        // IF node on the condition the previous chunk set
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = mine;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, root, &prev, nullptr, 1, &cp);
+        if (e == cudaSuccess) {
+          cudaGraphNode_t inner = nullptr;
+          e = add_child(cp.conditional.phGraph_out[0], g, nullptr, &inner);
+        }
+      }
+      prev = node;
+    }
+    b->checks[i] = check;
+    for (int s = 0; s < kNumStages; ++s) {
+      b->launches[i][s] = h->stage_launches[s] - before[s];
+      h->stage_launches[s] = before[s];   // counted per graph launch instead (upper bound)
+    }
+  }
+  for (auto g : parts) cudaGraphDestroy(g);
+  if (st == RIHV_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, root, 0);
+  cudaGraphDestroy(root);
+  if (st != RIHV_OK) return st;
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return fail(h0, RIHV_ERR_CUDA, "conditional batch graph: %s", cudaGetErrorString(e));
+  }
+  b->conditional = true;
+  b->iters = iters;
+  b->l1 = l1;
+  b->ltv = ltv;
+  b->warm = warm;
+  b->opts.clear();
+  b->tunes.clear();
+  for (auto* h : b->hs) {
+    b->opts.push_back(h->opt);
+    b->tunes.push_back(h->tv_zchunk);
+    b->tunes.push_back(h->zpg);
+  }
+  return RIHV_OK;
 }
 
 static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, bool warm) {
@@ -1013,6 +1171,7 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     b->exec = nullptr;
     return fail(h0, RIHV_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
+  b->conditional = false;
   b->iters = iters;
   b->l1 = l1;
   b->ltv = ltv;
@@ -1038,14 +1197,14 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
     rihv_ctx* h = b->hs[i];
     if (!holograms[i] || !x_outs[i]) return fail(h, RIHV_ERR_INVALID_ARG, "null hologram or x_out");
     CKS(check_solve_args(h, lambda_l1, lambda_tv, iters));
-    if (h->opt.f_star > 0.0)
-      return fail(h, RIHV_ERR_INVALID_ARG, "batched solves run a fixed iteration count (f_star must be 0)");
     const int M = h->opt.check_every;
     CKS(ensure_trace(h, (M > 0) ? iters / M : 0));
   }
+  bool cond = false;   // some hologram has a stop test: graph with IF nodes
+  for (auto* h : b->hs) cond = cond || (h->opt.f_star > 0.0 && h->opt.check_every > 0);
   const bool warm = x0s != nullptr;
   bool recapture = !b->exec || b->iters != iters || b->l1 != lambda_l1 || b->ltv != lambda_tv ||
-                   b->warm != warm;
+                   b->warm != warm || b->conditional != cond;
   for (int i = 0; i < n && !recapture; ++i) {
     rihv_ctx* h = b->hs[i];
     recapture = !same_options(b->opts[i], h->opt) || b->tunes[2 * i] != h->tv_zchunk ||
@@ -1060,8 +1219,15 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
       CK(cudaMemcpyAsync(h->x, x0s[i], h->nvox * sizeof(float2), cudaMemcpyDefault, b->master));
     }
   }
-  if (recapture) CKS(batch_capture(b, lambda_l1, lambda_tv, iters, warm));
+  if (recapture)
+    CKS(cond ? batch_capture_cond(b, lambda_l1, lambda_tv, iters, warm)
+             : batch_capture(b, lambda_l1, lambda_tv, iters, warm));
   rihv_ctx* h = h0;
+  if (cond) {   // objective checks a hologram does not reach read as NaN
+    for (int i = 0; i < n; ++i)
+      if (b->checks[i] > 0)
+        CK(cudaMemsetAsync(b->hs[i]->trace, 0xFF, sizeof(double) * b->checks[i], b->master));
+  }
   CK(cudaGraphLaunch(b->exec, b->master));
   for (int i = 0; i < n; ++i) {
     rihv_ctx* hi = b->hs[i];
@@ -1071,8 +1237,18 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
       CK(cudaMemcpyAsync(traces[i], hi->trace, sizeof(double) * b->checks[i], cudaMemcpyDefault,
                          b->master));
   }
+  if (cond)
+    CK(cudaMemcpyAsync(b->done.data(), b->done_dev, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                       b->master));
   CK(cudaStreamSynchronize(b->master));
+  if (!cond) std::fill(b->done.begin(), b->done.end(), iters);
   for (auto* hi : b->hs) CKS(read_solve_errors(hi));
+  return RIHV_OK;
+}
+
+rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done) {
+  if (!b || !iters_done) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null argument");
+  for (size_t i = 0; i < b->done.size(); ++i) iters_done[i] = b->done[i];
   return RIHV_OK;
 }
 

@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_batch_solve": (i, [H, ctypes.POINTER(vp), f, f, i, ctypes.POINTER(vp),
                                  ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "rihv_batch_destroy": (i, [H]),
+        "rihv_batch_iterations": (i, [H, ctypes.POINTER(i)]),
         "rihv_autotune": (i, [H, ctypes.c_char_p, ctypes.POINTER(i)]),
         "rihv_coo_compact": (i, [H, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_longlong)]),
@@ -323,6 +324,15 @@ class Batch:
         if st != 0:
             msgs = [self.L.rihv_last_error(h.h).decode() for h in self.handles]
             raise RihvError(st, "; ".join(m for m in msgs if m))
+
+    def iterations(self):
+        """Iterations each handle ran in the last solve (handles with a stop
+        test, f_star > 0, stop at their first check that meets it)."""
+        out = (ctypes.c_int * len(self.handles))()
+        st = self.L.rihv_batch_iterations(self.b, out)
+        if st != 0:
+            raise RihvError(st, "rihv_batch_iterations failed")
+        return list(out)
 
     def close(self):
         if getattr(self, "b", None):

@@ -74,13 +74,47 @@ def test_batch_matches_oracle_and_host_buffers():
     batch.close()
 
 
-def test_batch_rejects_stop_test_and_duplicates():
+def test_batch_stop_tests_inside_the_graph():
+    """Handles with a stop test (f_star > 0) stop inside the batched graph at
+    the same check as rihv_solve, with bitwise the same volume and trace; a
+    handle without one runs all iterations; replaying the graph is stable."""
+    dev = torch.device("cuda:0")
+    probs = [_problem(*s, seed=50 + i) for i, s in enumerate(SHAPES)]
+    f_star = []
+    for op, b in probs:                       # reference objective: 60 iterations
+        h = _handle(op, check_every=5)
+        x = torch.empty(op.shape, dtype=torch.complex64, device=dev)
+        tr = np.zeros(12)
+        h.solve(b, 0.01, 0.005, 60, x, trace=tr)
+        f_star.append(float(tr.min()))
+    tols = [1e-2, 1e-3, None]                 # the last handle: no stop test
+    hs, ref = [], []
+    for (op, b), fs, tol in zip(probs, f_star, tols):
+        opts = dict(check_every=5) if tol is None else dict(check_every=5, f_star=fs, tol=tol)
+        h = _handle(op, **opts)
+        x = torch.empty(op.shape, dtype=torch.complex64, device=dev)
+        tr = np.full(8, np.nan)
+        done = h.solve(b, 0.01, 0.005, 40, x, trace=tr)
+        hs.append(h)
+        ref.append((done, x.clone(), tr))
+    assert ref[0][0] < 40 and ref[2][0] == 40
+    batch = Batch(hs)
+    for rep in range(2):
+        outs = [torch.empty(op.shape, dtype=torch.complex64, device=dev) for op, _ in probs]
+        trs = [np.zeros(8) for _ in probs]
+        batch.solve([b for _, b in probs], 0.01, 0.005, 40, outs, traces=trs)
+        its = batch.iterations()
+        for (done, xr, trr), o, t, it in zip(ref, outs, trs, its):
+            assert it == done
+            assert torch.equal(o, xr)
+            n = done // 5
+            assert np.array_equal(t[:n], trr[:n]) and np.all(np.isnan(t[n:]))
+    batch.close()
+
+
+def test_batch_rejects_duplicates():
     op, b = _problem(*SHAPES[0], seed=1)
-    h = _handle(op, check_every=10, f_star=1.0, tol=0.1)
-    batch = Batch([h])
-    x = torch.empty(op.shape, dtype=torch.complex64, device="cuda:0")
-    with pytest.raises(RihvError):
-        batch.solve([b], 0.01, 0.005, 10, [x])
+    h = _handle(op, check_every=10)
     with pytest.raises(RihvError):
         Batch([h, h])
 
