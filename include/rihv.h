@@ -57,7 +57,7 @@ typedef enum {
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
- * tv_steps_per_launch 2, fuse_finalize 1. */
+ * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -70,13 +70,26 @@ typedef struct {
   int tv_steps_per_launch; /* 1: one dual step per kernel launch; 2: two
                         steps per launch (same arithmetic, the first step
                         recomputed on a one-voxel halo ring; an odd step
-                        count ends with a one-step launch). 2 needs nx even,
-                        which every supported size is.                       */
-  int fuse_finalize; /* 1: with two steps per launch and an even step count,
-                        the last TV launch also forms x = soft(v - mu D^H p)
+                        count starts with a one-step launch). 2 needs nx
+                        even, which every supported size is.                 */
+  int fuse_finalize; /* 1: with two steps per launch and >= 2 steps, the
+                        last TV launch also forms x = soft(v - mu D^H p)
                         (and FISTA's y and restart product), so the final
                         dual never reaches memory; 0: separate finalize
                         kernel. Same arithmetic either way.                  */
+  int skip_empty_planes; /* 1: the fused finalize records which planes of
+                        x_k and y_{k+1} hold a non-zero voxel, and the next
+                        forward propagations (of y_{k+1}, and of x_k for the
+                        objective) skip the 2D FFTs and z-sum terms of the
+                        all-zero planes (Section 2: the volume is sparse and
+                        each plane propagates independently). Exact: a zero
+                        plane adds nothing to the sum. Off by default: the
+                        recording costs the finalize launch a few per cent
+                        and pays only where solutions leave whole planes
+                        empty. Takes effect when the finalize is fused
+                        (fuse_finalize 1, two steps per launch, n_inner >= 2,
+                        lambda_tv > 0) and nx, ny <= 1024; otherwise every
+                        plane is propagated.                                 */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */

@@ -23,6 +23,8 @@
 // conj(H_j) R in registers for every plane and inverse-transforms it.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "rihv_internal.cuh"
 
 namespace rihv {
@@ -500,39 +502,53 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_rows_reg(const __grid_c
       }
     }
   };
-  // the next item's loads are issued before this item's transform
-  float2 nxt[8];
-  if (blockIdx.x < nitems) load(blockIdx.x, nxt);
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int row = (item % rblocks) * NT + team;
-    const size_t z = item / rblocks;
-    float2 v[8];
+  // Items of planes marked all-zero are skipped (the same for the whole CTA).
+  // The flags are read only when some plane is marked; otherwise the plain
+  // instance of the loop runs, with no flag reads in it.
+  const int* occ = (IN != ROW_IN_STRIP && a.occ && __ldg(a.occ + a.nz) != 0) ? a.occ : nullptr;
+  auto run = [&](auto skip) {
+    constexpr bool SKIP = decltype(skip)::value;
+    auto live = [&](int item) { return !SKIP || __ldg(occ + item / rblocks) != 0; };
+    // the next item's loads are issued before this item's transform
+    float2 nxt[8];
+    if (blockIdx.x < nitems && live(blockIdx.x)) load(blockIdx.x, nxt);
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+      const int row = (item % rblocks) * NT + team;
+      const size_t z = item / rblocks;
+      const bool here = live(item);
+      float2 v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = nxt[e];
-    if (item + gridDim.x < nitems) load(item + gridDim.x, nxt);
-    // the gradient step's y is loaded before the transform, so that its
-    // latency overlaps the transform and no store waits on a load
-    float2 yv[8];
-    if (OUT != ROW_OUT_STRIP && EPI == ROW_EPI_GRAD) {
+      for (int e = 0; e < 8; ++e) v[e] = nxt[e];
+      if (item + gridDim.x < nitems && live(item + gridDim.x)) load(item + gridDim.x, nxt);
+      if (!here) continue;
+      // the gradient step's y is loaded before the transform, so that its
+      // latency overlaps the transform and no store waits on a load
+      float2 yv[8];
+      if (OUT != ROW_OUT_STRIP && EPI == ROW_EPI_GRAD) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) yv[e] = a.y[(z * a.ny + row) * N + i + TT * e];
-    }
-    rfft<N, INV>(v, i, xa, xb, tw);
+        for (int e = 0; e < 8; ++e) yv[e] = a.y[(z * a.ny + row) * N + i + TT * e];
+      }
+      rfft<N, INV>(v, i, xa, xb, tw);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int c = i + TT * e;
-      if (OUT == ROW_OUT_STRIP) {
-        a.dst[((z * nstrip + c / W) * a.ny + row) * W + (c % W)] = cscale(v[e], a.scale);
-      } else {
-        const size_t gi = (z * a.ny + row) * N + c;
-        if (EPI == ROW_EPI_GRAD) {
-          a.dst[gi] = make_float2(yv[e].x - a.scale * v[e].x, yv[e].y - a.scale * v[e].y);
+      for (int e = 0; e < 8; ++e) {
+        const int c = i + TT * e;
+        if (OUT == ROW_OUT_STRIP) {
+          a.dst[((z * nstrip + c / W) * a.ny + row) * W + (c % W)] = cscale(v[e], a.scale);
         } else {
-          a.dst[gi] = cscale(v[e], a.scale);
+          const size_t gi = (z * a.ny + row) * N + c;
+          if (EPI == ROW_EPI_GRAD) {
+            a.dst[gi] = make_float2(yv[e].x - a.scale * v[e].x, yv[e].y - a.scale * v[e].y);
+          } else {
+            a.dst[gi] = cscale(v[e], a.scale);
+          }
         }
       }
     }
-  }
+  };
+  if (occ)
+    run(std::true_type{});
+  else
+    run(std::false_type{});
 }
 
 // Column pass, register engine: one strip of kStrip columns (team = column),
@@ -569,24 +585,56 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
       float2 acc[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] = make_float2(0.f, 0.f);
+      // Planes marked all-zero add nothing and are passed over (CTA-uniform).
+      // The flags are read only when some plane is marked; otherwise the
+      // plain loop runs.
+      const int* occ = (a.occ && __ldg(a.occ + a.nz) != 0) ? a.occ : nullptr;
       float2 nxt[8];   // the next plane's loads are issued before this plane's transform
-      if (z0 < z1) {
-        const float2* src = a.src + (static_cast<size_t>(z0) * nstrip + s) * strip_elems;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
-      }
-      for (int z = z0; z < z1; ++z) {
-        float2 v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = nxt[e];
-        if (z + 1 < z1) {
-          const float2* src = a.src + (static_cast<size_t>(z + 1) * nstrip + s) * strip_elems;
+      if (!occ) {
+        if (z0 < z1) {
+          const float2* src = a.src + (static_cast<size_t>(z0) * nstrip + s) * strip_elems;
 #pragma unroll
           for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
         }
-        rfft<N, false>(v, i, xa, xb, tw);
+        for (int z = z0; z < z1; ++z) {
+          float2 v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+          for (int e = 0; e < 8; ++e) v[e] = nxt[e];
+          if (z + 1 < z1) {
+            const float2* src = a.src + (static_cast<size_t>(z + 1) * nstrip + s) * strip_elems;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
+          }
+          rfft<N, false>(v, i, xa, xb, tw);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+        }
+      } else {
+        auto next_live = [&](int z) {
+          while (z < z1 && __ldg(occ + z) == 0) ++z;
+          return z;
+        };
+        int z = next_live(z0);
+        if (z < z1) {
+          const float2* src = a.src + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
+        }
+        while (z < z1) {
+          float2 v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = nxt[e];
+          const int zn = next_live(z + 1);
+          if (zn < z1) {
+            const float2* src = a.src + (static_cast<size_t>(zn) * nstrip + s) * strip_elems;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) nxt[e] = src[(i + TT * e) * W + w];
+          }
+          rfft<N, false>(v, i, xa, xb, tw);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+          z = zn;
+        }
       }
       float2* dst = a.dst + static_cast<size_t>(blockIdx.y) * a.nx * a.ny;
 #pragma unroll
@@ -713,9 +761,6 @@ cudaError_t launch_cols_reg(const ColArgs& a, int groups, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Lengths served by the register engine.
-bool reg_length(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
-
 template <bool INV, int IN, int OUT, int EPI>
 cudaError_t launch_rows_t(const RowArgs& a, cudaStream_t s) {
   switch (a.nx) {
@@ -761,6 +806,9 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Lengths served by the register engine.
+bool reg_length(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
 
 size_t rows_smem_bytes(int nx) {
   if (reg_length(nx)) return sizeof(float2) * (nx + 2 * 4 * static_cast<size_t>(nx + 4));

@@ -105,6 +105,7 @@ struct rihv_ctx {
   long long* coo_seg_off = nullptr;  // their exclusive offsets
   int* coo_bad = nullptr;            // set by the COO scatter for an entry off the plane
   int* tv_err = nullptr;       // set by a TV kernel whose bounded wait gave up
+  int* occ = nullptr;          // [nz] planes of x_k / y_{k+1} with a non-zero voxel
   CUtensorMap tm_pa[3][3], tm_pb[3][3];   // [one-step, two-step, fused-finalize box]
   DetectWork det{};
   std::vector<void*> allocs;
@@ -266,12 +267,17 @@ ColArgs col_args(rihv_ctx* h, const float2* src, float2* dst) {
 }
 
 // Spectrum of the modelled hologram S = sum_j H_j F x_j; with bhat, the
-// residual spectrum R = S - F b and ||Hx - b||^2 -> sc->rnorm2.
-rihv_status forward_spectrum(rihv_ctx* h, const float2* xin, const float2* bhat, float2* out) {
+// residual spectrum R = S - F b and ||Hx - b||^2 -> sc->rnorm2. With occ
+// (plane occupancy of xin), planes marked 0 are all-zero and skipped.
+rihv_status forward_spectrum(rihv_ctx* h, const float2* xin, const float2* bhat, float2* out,
+                             const int* occ = nullptr) {
   StageScope sc(h, ST_FORWARD, 3);
-  CK(launch_rows(0, ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE, row_args(h, xin, h->inter, h->nz),
-                 h->stream));
-  CK(launch_cols(COL_FWD_ZSUM, col_args(h, h->inter, h->partial), h->groups, h->stream));
+  RowArgs ra = row_args(h, xin, h->inter, h->nz);
+  ColArgs ca = col_args(h, h->inter, h->partial);
+  ra.occ = occ;
+  ca.occ = occ;
+  CK(launch_rows(0, ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE, ra, h->stream));
+  CK(launch_cols(COL_FWD_ZSUM, ca, h->groups, h->stream));
   CK(launch_zsum(h->partial, h->groups, bhat, out, h->nx, h->ny, h->sc, h->red, h->stream));
   return RIHV_OK;
 }
@@ -298,15 +304,15 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
 }
 
 // K dual steps; returns the buffer set holding the final p. With `fin` (two
-// steps per launch, K even) the last launch also runs the finalize and
+// steps per launch, K >= 2) the last launch also runs the finalize and
 // *pfinal is null.
 rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal,
                      const FinArgs* fin = nullptr, int fin_mode = FIN_PROX) {
-  // With tv_steps_per_launch = 2, two dual steps per launch and a single-step
-  // launch for an odd remainder.
+  // With tv_steps_per_launch = 2, two dual steps per launch; an odd K starts
+  // with a single-step launch, so that the last launch is always a pair.
   const int per = h->opt.tv_steps_per_launch;
   const int launches = per == 2 ? k / 2 + (k % 2) : k;
-  const bool fused = fin && per == 2 && k >= 2 && k % 2 == 0;
+  const bool fused = fin && per == 2 && k >= 2;
   StageScope sc(h, ST_TV, launches);
   CUtensorMap tm_v[3];
   CK(make_volume_tmap(&tm_v[0], v, h->nx, h->ny, h->nz, kTvBoxH1, kTvBoxW));
@@ -332,25 +338,29 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
     a.sc = fin->sc;
     a.fin_partials = h->fin_partials;
     a.fin_ticket = h->red.tickets + 3;
+    if (fin_mode == FIN_FISTA && h->opt.skip_empty_planes) a.occ = h->occ;
   }
   float2** src = h->pb;
   float2** dst = h->pa;
   bool src_is_b = true;
   int done = 0;
   while (done < k) {
-    const int n = (per == 2 && k - done >= 2) ? 2 : 1;
+    const int n = (per == 2 && !(done == 0 && k % 2 == 1)) ? 2 : 1;
     const bool last = done + n == k;
     const int b = n == 2 ? ((fused && last) ? 2 : 1) : 0;
     // the fused-finalize launch has its own tile, so its own default chunk
     a.zchunk = (fused && last) ? zc_final
                                : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32));
-    if (fused && last && tv_final_ctas(h->nx, h->ny, h->nz, a.zchunk) > h->fin_ctas)
-      return fail(h, RIHV_ERR_INVALID_ARG, "z-chunk too small for the fused finalize");
+    if (fused && last && (tv_final_ctas(h->nx, h->ny, h->nz, a.zchunk) > h->fin_ctas ||
+                          a.zchunk > kTvMaxChunk))
+      return fail(h, RIHV_ERR_INVALID_ARG, "z-chunk outside the fused finalize's range");
     a.tm_v = tm_v[b];
     for (int c = 0; c < 3; ++c) {
       a.tm_p[c] = src_is_b ? h->tm_pb[b][c] : h->tm_pa[b][c];
       a.pout[c] = dst[c];
     }
+    if (fused && last && a.occ)
+      CK(cudaMemsetAsync(a.occ, 0, sizeof(int) * (h->nz + 1), h->stream));
     {
       StageScope sub(h, (fused && last) ? ST_TV_FINAL : (done == 0 ? ST_TV_FIRST : ST_TV_MID), 1, 2);
       CK(launch_tv_step(done == 0, n, a, h->stream, fused && last));
@@ -415,6 +425,15 @@ void choose_groups(rihv_ctx* h, int nz) {
   h->groups = (nz + best_zpg - 1) / best_zpg;
 }
 
+// Whether a FISTA iteration with TV weight t_tv (already times the step)
+// leaves the plane occupancy of x_k and y_{k+1} in h->occ: only the fused
+// finalize records it, and only the register FFT engine reads it.
+bool occ_tracked(const rihv_ctx* h, float t_tv) {
+  const int k = h->opt.n_inner;
+  return h->opt.skip_empty_planes && h->opt.fuse_finalize && h->opt.tv_steps_per_launch == 2 &&
+         t_tv > 0.f && k >= 2 && reg_length(h->nx) && reg_length(h->ny);
+}
+
 rihv_status copy_in(rihv_ctx* h, void* dst, const void* src, size_t bytes) {
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
   return RIHV_OK;
@@ -465,6 +484,10 @@ rihv_status enqueue_setup(rihv_ctx* h, bool warm) {
   const size_t vb = h->nvox * sizeof(float2);
   if (!warm) CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
   CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
+  // occupancy of y_1 = x_0: no plane from zero, every plane from a warm
+  // start; occ[nz] = some plane empty
+  CK(cudaMemsetAsync(h->occ, warm ? 1 : 0, sizeof(int) * h->nz, h->stream));
+  CK(cudaMemsetAsync(h->occ + h->nz, warm ? 0 : 1, sizeof(int), h->stream));
   CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
   CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
   return RIHV_OK;
@@ -476,15 +499,17 @@ rihv_status enqueue_setup(rihv_ctx* h, bool warm) {
 rihv_status enqueue_iteration(rihv_ctx* h, int k, float lambda_l1, float lambda_tv, int* check) {
   const float tau = static_cast<float>(h->tau);
   const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
+  // planes of y_k (and of x_k below) that are all zero skip the forward
+  const int* occ = occ_tracked(h, tau * lambda_tv) ? h->occ : nullptr;
   // (a) forward and residual spectrum R = F(H y - b)
-  CKS(forward_spectrum(h, h->y, h->bhat, h->spec));
+  CKS(forward_spectrum(h, h->y, h->bhat, h->spec, occ));
   // (c) v = y - tau * 2 H^H r
   CKS(adjoint_planes(h, h->spec, h->y, h->v, grad_scale, true));
   // (d) x_k = prox(v), momentum, restart
   CKS(prox_into(h, h->v, tau * lambda_l1, tau * lambda_tv, h->opt.n_inner, FIN_FISTA, h->x));
   const int M = h->opt.check_every;
   if (M > 0 && k % M == 0) {
-    CKS(forward_spectrum(h, h->x, h->bhat, h->spec));
+    CKS(forward_spectrum(h, h->x, h->bhat, h->spec, occ));
     StageScope sc(h, ST_OBJECTIVE, 1);
     CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, lambda_l1, lambda_tv, h->sc,
                         h->red, h->trace + *check, h->stream));
@@ -522,6 +547,7 @@ void rihv_default_options(rihv_options* o) {
   o->f_star = 0.0;
   o->tv_steps_per_launch = 2;
   o->fuse_finalize = 1;
+  o->skip_empty_planes = 0;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -590,6 +616,7 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   AL(h->coo_seg_off, static_cast<size_t>(nz) * coo_segments(nx, ny));
   AL(h->coo_bad, 1);
   AL(h->tv_err, 1);
+  AL(h->occ, h->nz + 1);
 #undef AL
   if (cudaMemset(h->red.tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(h->det_err, 0, sizeof(int)) != cudaSuccess ||
@@ -681,7 +708,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       o->tol < 0 || o->f_star < 0 || (o->restart != 0 && o->restart != 1) ||
       (o->accelerate != 0 && o->accelerate != 1) ||
       (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2) ||
-      (o->fuse_finalize != 0 && o->fuse_finalize != 1))
+      (o->fuse_finalize != 0 && o->fuse_finalize != 1) ||
+      (o->skip_empty_planes != 0 && o->skip_empty_planes != 1))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   h->opt = *o;
   return RIHV_OK;
@@ -981,7 +1009,7 @@ static bool same_options(const rihv_options& a, const rihv_options& o) {
   return a.tv_dims == o.tv_dims && a.restart == o.restart && a.accelerate == o.accelerate &&
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
          a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
-         a.f_star == o.f_star && a.tol == o.tol;
+         a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes;
 }
 
 // Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a

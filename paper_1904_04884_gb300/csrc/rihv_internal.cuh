@@ -37,6 +37,7 @@ constexpr int kTv2Threads = 32 * kTv2Warps;
 constexpr int kTv2BoxW = kTv2Tx + 4;
 constexpr int kTv2BoxH = kTv2Ty + 4;
 constexpr int kTv2Stages = 3;
+constexpr int kTvMaxChunk = 256;   // largest z-chunk of a fused-finalize TV launch
 // The launch with the fused finalize needs one more halo ring on the low
 // sides (D^H of the final dual): a 58 x 11 tile, box 64 x 16 from (i0-4,
 // j0-3), 15 warps (fewer threads leave room for its extra per-thread state).
@@ -90,6 +91,9 @@ struct RowArgs {
   float scale;         // ROW_EPI_SCALE: out = scale * g; ROW_EPI_GRAD: v = y - scale * g
   FftPlan plan;        // along x
   const float2* tw;    // twiddles exp(-2 pi i m / nx), m < nx
+  const int* occ;      // forward rows (complex input): [nz + 1] plane occupancy; when
+                       // occ[nz] != 0, planes z with occ[z] == 0 are all zero and
+                       // skipped (nothing written); null: every plane
 };
 
 enum ColMode { COL_FWD_ZSUM = 0, COL_ADJ_GEN = 1, COL_PLAIN_FWD = 2, COL_PLAIN_INV = 3 };
@@ -104,6 +108,8 @@ struct ColArgs {
   float scale;
   FftPlan plan;        // along y
   const float2* tw;    // twiddles exp(-2 pi i m / ny), m < ny
+  const int* occ;      // COL_FWD_ZSUM: [nz + 1] plane occupancy as for the rows; skipped
+                       // planes are left out of the z-sum; null: every plane
 };
 
 cudaError_t launch_rows(int dir_inverse, int in, int out, int epi, const RowArgs& a,
@@ -111,6 +117,7 @@ cudaError_t launch_rows(int dir_inverse, int in, int out, int epi, const RowArgs
 cudaError_t launch_cols(int mode, const ColArgs& a, int groups, cudaStream_t s);
 size_t rows_smem_bytes(int nx);
 size_t cols_smem_bytes(int mode, int ny);
+bool reg_length(int n);   // lengths served by the register FFT engine
 // Resident CTAs per SM of the forward column pass for this ny (sizes the z-groups).
 int cols_ctas_per_sm(int ny);
 
@@ -143,6 +150,9 @@ struct TvArgs {
   DevScalars* sc;
   double* fin_partials;   // one double per CTA of the launch
   unsigned* fin_ticket;   // last-block counter (reset by the last block)
+  int* occ;               // FISTA: [nz + 1], zeroed before the launch; occ[z] set for
+                          // every plane z with a non-zero voxel of x_k or y_{k+1},
+                          // occ[nz] = 1 if some plane has none; or null
 };
 // nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero;
 // final (two-step launches only): fused finalize, no dual output.
@@ -159,6 +169,7 @@ cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, 
                              int box_rows, int box_cols);
 
 enum FinMode { FIN_PROX = 0, FIN_FISTA = 1 };
+constexpr int kFinFistaOcc = 2;   // fused-finalize kernel variant: FISTA + plane occupancy
 struct FinArgs {
   const float2* v;
   const float2* p[3];  // may be null (no TV): u = v

@@ -445,10 +445,13 @@ __device__ __forceinline__ float4 pack4(float2 a, float2 b) { return make_float4
 //   (e) x(t-1) = soft(v - mu D^H p^2, kappa)   [p^2(t-1), p^2_z(t-2)]
 // is written instead of p^2, in FISTA mode with y_{k+1} = x + beta (x -
 // x_prev) and the restart inner product, reduced like the finalize kernel.
+// FMODE: FIN_PROX, FIN_FISTA, or kFinFistaOcc (FISTA that also records
+// which planes hold a non-zero voxel, for the empty-plane skip).
 template <bool FIRST, bool FINAL, int FMODE = FIN_PROX>
 __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
     k_tv_step2(const __grid_constant__ TvArgs a) {
-  constexpr bool FISTA = FINAL && FMODE == FIN_FISTA;
+  constexpr bool FISTA = FINAL && (FMODE == FIN_FISTA || FMODE == kFinFistaOcc);
+  constexpr bool OCC = FINAL && FMODE == kFinFistaOcc;
   constexpr int TXk = FINAL ? kTv2TxF : kTv2Tx;
   constexpr int TYk = FINAL ? kTv2TyF : kTv2Ty;
   constexpr int NW2 = FINAL ? kTv2WarpsF : kTv2Warps;
@@ -495,6 +498,10 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
   const float2 syhi = splat(gy <= a.ny - 2 ? a.step : 0.f);
   const float2 nmu = splat(-a.mu);
 
+  // OCC: which planes of the chunk hold a non-zero voxel of x_k or y_{k+1}
+  __shared__ unsigned char occ_s[OCC ? kTvMaxChunk : 1];
+  if (OCC)
+    for (int q = tid; q < kTvMaxChunk; q += blockDim.x) occ_s[q] = 0;
   if (tid == 0) {
     for (int s = 0; s < kTv2Stages; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -678,6 +685,7 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
           }
           xv[e] = soft_rsqrt(x2fma(nmu, dh, v_prev[e]), a.kappa);
         }
+        unsigned bits = 0u;     // OCC: any non-zero component (sign bits masked below)
         if (out_pair) {
           const size_t gidx = (static_cast<size_t>(qf) * a.ny + gy) * a.nx + gx0;
           if (FISTA) {
@@ -692,9 +700,17 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
             }
             if (++dot_cnt == 4) { dot_sum += dot_local; dot_local = 0.f; dot_cnt = 0; }
             *reinterpret_cast<float4*>(a.y_out + gidx) = pack4(yo[0], yo[1]);
+            if (OCC)
+              bits = __float_as_uint(xv[0].x) | __float_as_uint(xv[0].y) |
+                     __float_as_uint(xv[1].x) | __float_as_uint(xv[1].y) |
+                     __float_as_uint(yo[0].x) | __float_as_uint(yo[0].y) |
+                     __float_as_uint(yo[1].x) | __float_as_uint(yo[1].y);
           }
           *reinterpret_cast<float4*>(a.x_out + gidx) = pack4(xv[0], xv[1]);
         }
+        // plane occupancy for the next forward (same value from every writer)
+        if (OCC && __any_sync(0xffffffffu, (bits & 0x7fffffffu) != 0u) && lane == 0)
+          occ_s[qf - zc0] = 1;
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -719,9 +735,16 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
     // restart inner product: FP32 over at most 8 voxels, FP64 above; fixed-
     // order sum over the CTAs by the last one, which updates t and beta
     dot_sum += dot_local;
-    const double bs = block_sum(dot_sum);
+    const double bs = block_sum(dot_sum);      // (its barriers also publish occ_s)
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (OCC) {
+      if (tid < zc1 - zc0 && occ_s[tid]) {
+        a.occ[zc0 + tid] = 1;
+        __threadfence();
+      }
+      __syncthreads();
+    }
     __shared__ bool last;
     if (tid == 0) {
       a.fin_partials[bid] = bs;
@@ -737,6 +760,15 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
     if (tid == 0) {
       fista_update(a.sc, dot);
       *a.fin_ticket = 0;
+    }
+    if (OCC) {
+      // occ[nz] = 1 when some plane is all zero (the forward then reads the
+      // per-plane flags; otherwise it propagates every plane unchecked)
+      int empty = 0;
+      for (int q = tid; q < a.nz; q += blockDim.x)
+        empty |= static_cast<volatile int*>(a.occ)[q] == 0;
+      empty = __syncthreads_or(empty);
+      if (tid == 0) a.occ[a.nz] = empty;
     }
   }
 }
@@ -899,8 +931,10 @@ cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t
   dim3 grid((a.nx + tx - 1) / tx, (a.ny + ty - 1) / ty, (a.nz + a.zchunk - 1) / a.zchunk);
   const bool fista = a.fin_mode == FIN_FISTA;
   auto kern = nsteps == 2
-                  ? (final ? (fista ? (first ? k_tv_step2<true, true, FIN_FISTA>
-                                             : k_tv_step2<false, true, FIN_FISTA>)
+                  ? (final ? (fista ? (a.occ ? (first ? k_tv_step2<true, true, kFinFistaOcc>
+                                                      : k_tv_step2<false, true, kFinFistaOcc>)
+                                             : (first ? k_tv_step2<true, true, FIN_FISTA>
+                                                      : k_tv_step2<false, true, FIN_FISTA>))
                                     : (first ? k_tv_step2<true, true> : k_tv_step2<false, true>))
                            : (first ? k_tv_step2<true, false> : k_tv_step2<false, false>))
                   : (first ? k_tv_step<true> : k_tv_step<false>);

@@ -41,6 +41,7 @@ class Workload:
     fibre_width_um: float = 3.0
     seed: int = 0
     tv_dims: int = 3
+    z_slab: tuple = ()       # (lo, hi): discs only on planes lo..hi-1; () = all planes
     extra: dict = field(default_factory=dict)
 
     @property
@@ -54,13 +55,23 @@ class Workload:
     def optics_tuple(self):
         return (self.nx, self.ny, self.nz, self.wavelength, self.pitch, self.z0, self.dz)
 
+    def _draw_discs(self, st: "synth.Stream") -> "synth.Particles":
+        lo, hi = self.z_slab or (0, self.nz)
+        parts = synth.random_discs(st, (hi - lo, self.ny, self.nx), self.n_discs,
+                                   self.d_um[0], self.d_um[1], self.pitch * 1e6,
+                                   self.at_voxel_centres)
+        parts.z += lo
+        return parts
+
+    def discs(self) -> "synth.Particles":
+        """The placed discs (the same draws ``opacity`` rasterises)."""
+        return self._draw_discs(synth.Stream(self.seed))
+
     def opacity(self) -> np.ndarray:
         """The seeded opacity volume a (float32 [nz][ny][nx])."""
         st = synth.Stream(self.seed)
         vol = np.zeros(self.shape, np.float32)
-        parts = synth.random_discs(st, self.shape, self.n_discs, self.d_um[0], self.d_um[1],
-                                   self.pitch * 1e6, self.at_voxel_centres)
-        synth.rasterise_discs(vol, parts)
+        synth.rasterise_discs(vol, self._draw_discs(st))
         if self.n_fibres:
             synth.rasterise_fibres(vol, st, self.n_fibres, self.fibre_len_um[0],
                                    self.fibre_len_um[1], self.fibre_width_um,
@@ -95,7 +106,16 @@ PAPER_TURBULENCE = Workload("paper_turbulence_512x512x700", 512, 512, 700, 632e-
                             at_voxel_centres=False, sigma=0.02, iters=100, lam_l1=0.5,
                             lam_tv=0.2, n_inner=20)
 
-ALL = {w.name: w for w in (TINY, MID, LARGE, PAPER_TURBULENCE)}
+# A thin particle layer inside a deeper reconstructed volume: 1,000 discs of
+# 10-20 um on planes 96-159 of 256 (a 3.2 mm layer in 12.8 mm of depth), with
+# the plane-wise TV, weights and 5 gradient-projection steps of the paper's
+# cuvette case (Section 3.3). Planes far from the layer can end up all zero,
+# which the forward propagation then skips.
+SLAB = Workload("slab_512x512x256", 512, 512, 256, 532e-9, 5e-6, 5e-3, 50e-6,
+                n_discs=1000, d_um=(10.0, 20.0), at_voxel_centres=False, sigma=0.02,
+                iters=100, lam_l1=0.1, lam_tv=0.1, n_inner=5, tv_dims=2, z_slab=(96, 160))
+
+ALL = {w.name: w for w in (TINY, MID, LARGE, PAPER_TURBULENCE, SLAB)}
 
 
 def shadow_density(n_per_volume: float, depth: float, diameter: float, area: float) -> float:

@@ -53,3 +53,17 @@ def test_default_options(lib):
     o = rihv.Options()
     lib.rihv_default_options(o)
     assert (o.tv_dims, o.restart, o.accelerate, o.n_inner, o.check_every) == (3, 1, 1, 20, 10)
+    assert (o.tv_steps_per_launch, o.fuse_finalize, o.skip_empty_planes) == (2, 1, 0)
+
+
+def test_options_binding_mirrors_the_header():
+    """The ctypes mirror lists the header's rihv_options fields in order."""
+    text = open(os.path.join(INC, "rihv.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} rihv_options;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int|double)\s+(\w+)\s*;", body)
+    names = [n for _, n in fields]
+    assert names == [n for n, _ in rihv.Options._fields_]
+    import ctypes
+    for (ty, _), (_, cty) in zip(fields, rihv.Options._fields_):
+        assert cty is (ctypes.c_int if ty == "int" else ctypes.c_double)
