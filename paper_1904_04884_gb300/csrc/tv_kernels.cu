@@ -773,6 +773,33 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
   }
 }
 
+// Coordinates (i, j, k) of a flat voxel index that advances by a fixed grid
+// stride: the stride is split into (si, sj, sk) once, so that each step is
+// two adds with a carry instead of 64-bit divisions.
+struct VoxelWalk {
+  size_t idx;
+  int i, j, k;
+  int si, sj, sk, nx, ny;
+  __device__ VoxelWalk(size_t start, size_t stride, int nx_, int ny_) : idx(start), nx(nx_), ny(ny_) {
+    i = static_cast<int>(start % nx);
+    j = static_cast<int>((start / nx) % ny);
+    k = static_cast<int>(start / (static_cast<size_t>(nx) * ny));
+    si = static_cast<int>(stride % nx);
+    sj = static_cast<int>((stride / nx) % ny);
+    sk = static_cast<int>(stride / (static_cast<size_t>(nx) * ny));
+  }
+  __device__ void advance(size_t stride) {
+    idx += stride;
+    i += si;
+    int c = i >= nx;
+    i -= c ? nx : 0;
+    j += sj + c;
+    c = j >= ny;
+    j -= c ? ny : 0;
+    k += sk + c;
+  }
+};
+
 // u = v - mu D^H p at voxel (i, j, k), straight from global memory.
 __device__ __forceinline__ float2 form_u(const FinArgs& a, size_t idx, int i, int j, int k) {
   float2 u = a.v[idx];
@@ -799,13 +826,11 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const __grid_constant_
   float local = 0.f;
   double dsum = 0.0;
   int cnt = 0;
-  for (size_t idx = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < nvox;
-       idx += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(idx % a.nx);
-    const size_t r = idx / a.nx;
-    const int j = static_cast<int>(r % a.ny);
-    const int k = static_cast<int>(r / a.ny);
-    const float2 x = soft(form_u(a, idx, i, j, k), a.kappa);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (VoxelWalk p(static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x, stride, a.nx, a.ny);
+       p.idx < nvox; p.advance(stride)) {
+    const size_t idx = p.idx;
+    const float2 x = soft(form_u(a, idx, p.i, p.j, p.k), a.kappa);
     if (MODE == FIN_FISTA) {
       const float2 xp = a.x_prev[idx];
       const float2 yk = a.y[idx];
@@ -842,12 +867,11 @@ __global__ void __launch_bounds__(kRedThreads) k_objective(const float2* x, int 
   float l1 = 0.f, tv = 0.f;
   double dl1 = 0.0, dtv = 0.0;
   int cnt = 0;
-  for (size_t idx = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < nvox;
-       idx += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(idx % nx);
-    const size_t r = idx / nx;
-    const int j = static_cast<int>(r % ny);
-    const int k = static_cast<int>(r / ny);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (VoxelWalk p(static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x, stride, nx, ny);
+       p.idx < nvox; p.advance(stride)) {
+    const size_t idx = p.idx;
+    const int i = p.i, j = p.j, k = p.k;
     const float2 c = x[idx];
     l1 += sqrtf(c.x * c.x + c.y * c.y);
     float g2 = 0.f;

@@ -84,7 +84,7 @@ def test_large_prox_on_crops(large, k):
     voxel depends on v within k + 1 voxels, so on a crop with an 8-voxel
     margin (none at the volume's own faces) the oracle's prox of the crop
     equals the full-size result. k = 4: first, then fused-final launch; k = 5:
-    first, one launch reading p, then the single step and the finalize kernel."""
+    a single first step, one launch reading p, then the fused-final launch."""
     op, h = large
     dev = torch.device("cuda:0")
     blk = synth.random_complex(synth.Stream(320), (32, 64, 64)).astype(np.complex64)
