@@ -413,6 +413,15 @@ __device__ __forceinline__ float2 shfl_up2(float2 v) {
   return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
 }
 
+// Adds v to the compensated sum (hi, lo) (Knuth's TwoSum: the rounding error
+// of hi + v goes to lo).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float b = s - hi;
+  lo += (hi - (s - b)) + (v - b);
+  hi = s;
+}
+
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 pack4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
@@ -522,9 +531,7 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
   float2 u1_prev[2] = {zero, zero}, u1_t[2] = {zero, zero};
   // FINAL: v of plane t-1 and p^2_z of plane t-2; FISTA restart partials
   float2 v_prev[2] = {zero, zero}, p2z_prev[2] = {zero, zero};
-  float dot_local = 0.f;
-  double dot_sum = 0.0;
-  int dot_cnt = 0;
+  float dot_hi = 0.f, dot_lo = 0.f;   // compensated FP32 sum of the restart product
   const float beta = FISTA ? static_cast<float>(a.sc->beta) : 0.f;
 
   // prologue: p^0_z of the ring's first plane (read by u^0 of the next)
@@ -692,13 +699,14 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
             const float2 xp[2] = {lo2(xp4), hi2(xp4)};
             const float2 yk[2] = {lo2(yk4), hi2(yk4)};
             float2 yo[2];
+            float d = 0.f;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
               const float2 dx = csub(xv[e], xp[e]);
-              dot_local += (yk[e].x - xv[e].x) * dx.x + (yk[e].y - xv[e].y) * dx.y;
+              d += (yk[e].x - xv[e].x) * dx.x + (yk[e].y - xv[e].y) * dx.y;
               yo[e] = make_float2(xv[e].x + beta * dx.x, xv[e].y + beta * dx.y);
             }
-            if (++dot_cnt == 4) { dot_sum += dot_local; dot_local = 0.f; dot_cnt = 0; }
+            two_sum_add(dot_hi, dot_lo, d);
             *reinterpret_cast<float4*>(a.y_out + gidx) = pack4(yo[0], yo[1]);
             if (OCC)
               bits = __float_as_uint(xv[0].x) | __float_as_uint(xv[0].y) |
@@ -732,10 +740,11 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
     }
   }
   if (FISTA) {
-    // restart inner product: FP32 over at most 8 voxels, FP64 above; fixed-
-    // order sum over the CTAs by the last one, which updates t and beta
-    dot_sum += dot_local;
-    const double bs = block_sum(dot_sum);      // (its barriers also publish occ_s)
+    // restart inner product: per thread a compensated FP32 sum over its
+    // voxels (no FP64 in the plane loop), FP64 across the block and a
+    // fixed-order sum over the CTAs by the last one, which updates t and beta
+    const double bs = block_sum(static_cast<double>(dot_hi) + static_cast<double>(dot_lo));
+    // (block_sum's barriers also publish occ_s)
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (OCC) {
@@ -859,30 +868,53 @@ __global__ void k_restart_fixup(const float2* x, float2* y, size_t nvox, const D
     y[idx] = x[idx];
 }
 
+// ||x||_1 and TV(x) (isotropic forward differences, Neumann boundary) in one
+// pass. Each item is four consecutive voxels of a row (nx is a multiple of
+// 8), read as 16-byte vectors together with the row below and the plane
+// below; per thread a compensated FP32 sum, FP64 across blocks.
 __global__ void __launch_bounds__(kRedThreads) k_objective(const float2* x, int nx, int ny, int nz,
                                                            int dims, double lam_l1, double lam_tv,
                                                            DevScalars* sc, RedWork w, double* f_out) {
-  const size_t nvox = static_cast<size_t>(nx) * ny * nz;
+  const int nq = nx / 4;
+  const size_t nitems = static_cast<size_t>(nq) * ny * nz;
   const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
-  float l1 = 0.f, tv = 0.f;
-  double dl1 = 0.0, dtv = 0.0;
-  int cnt = 0;
+  float l1h = 0.f, l1l = 0.f, tvh = 0.f, tvl = 0.f;
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-  for (VoxelWalk p(static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x, stride, nx, ny);
-       p.idx < nvox; p.advance(stride)) {
-    const size_t idx = p.idx;
-    const int i = p.i, j = p.j, k = p.k;
-    const float2 c = x[idx];
-    l1 += sqrtf(c.x * c.x + c.y * c.y);
-    float g2 = 0.f;
-    if (i <= nx - 2) { const float2 d = csub(x[idx + 1], c); g2 += d.x * d.x + d.y * d.y; }
-    if (j <= ny - 2) { const float2 d = csub(x[idx + sy], c); g2 += d.x * d.x + d.y * d.y; }
-    if (dims == 3 && k <= nz - 2) { const float2 d = csub(x[idx + sz], c); g2 += d.x * d.x + d.y * d.y; }
-    tv += sqrtf(g2);
-    if (++cnt == 8) { dl1 += l1; dtv += tv; l1 = 0.f; tv = 0.f; cnt = 0; }
+  for (VoxelWalk p(static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x, stride, nq, ny);
+       p.idx < nitems; p.advance(stride)) {
+    const int i = 4 * p.i, j = p.j, k = p.k;
+    const size_t idx = (static_cast<size_t>(k) * ny + j) * nx + i;
+    const float4* xv = reinterpret_cast<const float4*>(x + idx);
+    const float4 a0 = xv[0], a1 = xv[1];
+    const float2 c[5] = {lo2(a0), hi2(a0), lo2(a1), hi2(a1),
+                         i + 4 < nx ? x[idx + 4] : make_float2(0.f, 0.f)};
+    float2 ry[4], rz[4];
+    const bool hy = j <= ny - 2, hz = dims == 3 && k <= nz - 2;
+    if (hy) {
+      const float4* r = reinterpret_cast<const float4*>(x + idx + sy);
+      const float4 b0 = r[0], b1 = r[1];
+      ry[0] = lo2(b0); ry[1] = hi2(b0); ry[2] = lo2(b1); ry[3] = hi2(b1);
+    }
+    if (hz) {
+      const float4* r = reinterpret_cast<const float4*>(x + idx + sz);
+      const float4 b0 = r[0], b1 = r[1];
+      rz[0] = lo2(b0); rz[1] = hi2(b0); rz[2] = lo2(b1); rz[3] = hi2(b1);
+    }
+    float l1 = 0.f, tv = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      l1 += sqrtf(c[e].x * c[e].x + c[e].y * c[e].y);
+      float g2 = 0.f;
+      if (e < 3 || i + 4 < nx) { const float2 d = csub(c[e + 1], c[e]); g2 += d.x * d.x + d.y * d.y; }
+      if (hy) { const float2 d = csub(ry[e], c[e]); g2 += d.x * d.x + d.y * d.y; }
+      if (hz) { const float2 d = csub(rz[e], c[e]); g2 += d.x * d.x + d.y * d.y; }
+      tv += sqrtf(g2);
+    }
+    two_sum_add(l1h, l1l, l1);
+    two_sum_add(tvh, tvl, tv);
   }
-  dl1 += l1;
-  dtv += tv;
+  const double dl1 = static_cast<double>(l1h) + static_cast<double>(l1l);
+  const double dtv = static_cast<double>(tvh) + static_cast<double>(tvl);
   const double b1 = block_sum(dl1);
   const double b2 = block_sum(dtv);
   __shared__ bool last;

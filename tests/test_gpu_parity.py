@@ -328,3 +328,23 @@ def test_full_size_prox(mid):
     h.prox_fused_lasso(to_dev(v), 0.2, 0.05, 4, out)
     ref = O.prox_fused_lasso(v.astype(np.complex128), 0.2, 0.05, 4, 3)
     assert rel_l2(out.cpu().numpy(), ref) <= OP_TOL
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+@pytest.mark.parametrize("nx,ny,nz", [(16, 16, 1), (24, 48, 5), (64, 32, 9), (48, 16, 3)])
+def test_objective_of_the_iterate(nx, ny, nz, dims):
+    """F(x_1) as the solver reports it (vectorised objective pass, four voxels
+    of a row per item, ragged rows and planes at the volume faces) against the
+    oracle's objective of the same x_1."""
+    op = optics(nx, ny, nz)
+    b = np.real(synth.random_complex(synth.Stream(nx + ny + nz), (ny, nx))).astype(np.float32)
+    x0 = synth.random_complex(synth.Stream(nx * ny + nz), op.shape)
+    h = handle(op)
+    h.set_options(tv_dims=dims, n_inner=4, check_every=1)
+    x = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+    tr = np.zeros(1)
+    h.solve(b, 0.02, 0.01, 1, x, x0=to_dev(x0), trace=tr)
+    torch.cuda.synchronize()
+    xs = x.cpu().numpy().astype(np.complex128)
+    ref = O.objective(xs, b.astype(np.float64), op, 0.02, 0.01, dims)
+    assert abs(tr[0] - ref) <= 2e-5 * abs(ref)
