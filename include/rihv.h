@@ -266,6 +266,18 @@ rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out, int nx, in
                                           int tv_dims, float t_l1, float t_tv, int inner_iters,
                                           void* stream);
 
+/* Self-test of failure detection (no counterpart in the paper). Every wait
+ * of the library's kernels on an mbarrier (TMA tile arrival) is bounded: after
+ * a fixed number of polls the kernel records the failure in a device flag,
+ * lets its own copies in flight land (again bounded) and returns, and the
+ * calling entry point reports RIHV_ERR_TIMEOUT. This call runs that bounded
+ * wait on a barrier that nothing ever arrives on, with `polls` polls
+ * (1..2^22), on the handle's stream, and synchronises it. Expected result:
+ * RIHV_ERR_TIMEOUT, with the CUDA context still usable. RIHV_ERR_CUDA if the
+ * barrier completed or a CUDA call failed; RIHV_ERR_INVALID_ARG for polls out
+ * of range. */
+rihv_status rihv_selftest_bounded_wait(rihv_handle h, int polls);
+
 /* Per-stage timing. Kernel launches are always counted per stage. With
  * profiling level 1 (rihv_set_profiling(h, 1)) the library also records CUDA
  * events around its stages on the handle's stream; level 2 adds events around

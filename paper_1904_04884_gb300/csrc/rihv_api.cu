@@ -930,6 +930,20 @@ rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_
   return RIHV_OK;
 }
 
+rihv_status rihv_selftest_bounded_wait(rihv_handle h, int polls) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (polls < 1 || polls > (1 << 22))
+    return fail(h, RIHV_ERR_INVALID_ARG, "polls must be in [1, 2^22]");
+  int flag = 0;
+  CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
+  CK(launch_wait_selftest(h->tv_err, polls, h->stream));
+  CK(cudaMemcpyAsync(&flag, h->tv_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
+  if (flag) return fail(h, RIHV_ERR_TIMEOUT, "bounded wait gave up after %d polls (self-test)", polls);
+  return fail(h, RIHV_ERR_CUDA, "self-test barrier completed although nothing arrived on it");
+}
+
 rihv_status rihv_set_profiling(rihv_handle h, int on) {
   if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
   if (on && h->ev_pool.empty()) {

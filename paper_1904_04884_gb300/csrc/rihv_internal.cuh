@@ -190,6 +190,7 @@ cudaError_t launch_restart_fixup(const float2* x, float2* y, size_t nvox, const 
 cudaError_t launch_objective(const float2* x, int nx, int ny, int nz, int dims, double lam_l1,
                              double lam_tv, DevScalars* sc, RedWork w, double* f_out,
                              cudaStream_t s);
+cudaError_t launch_wait_selftest(int* flag, int polls, cudaStream_t s);
 cudaError_t launch_init_scalars(DevScalars* sc, int accelerate, int restart, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -69,9 +69,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: true if the phase completed, false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+// Bounded wait: true if the phase completed, false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1063,6 +1063,26 @@ cudaError_t launch_objective(const float2* x, int nx, int ny, int nz, int dims, 
   const size_t nvox = static_cast<size_t>(nx) * ny * nz;
   k_objective<<<stream_grid(nvox), kRedThreads, 0, s>>>(x, nx, ny, nz, dims, lam_l1, lam_tv, sc, w,
                                                          f_out);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded wait the TV kernels use: one warp waits on an
+// mbarrier that nothing arrives on (no copy is ever issued to it), gives up
+// after `polls` polls and records it in *flag as the TV kernels record a
+// failed wait in their error flag; the kernel then returns normally.
+__global__ void k_wait_selftest(int* flag, int polls) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(smem_addr(&bar), 0, polls);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) *flag = 1;
+}
+
+cudaError_t launch_wait_selftest(int* flag, int polls, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(flag, polls);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_coo_compact": (i, [H, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "rihv_coo_expand": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, vp]),
+        "rihv_selftest_bounded_wait": (i, [H, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -274,6 +275,12 @@ class Rihv:
     autotune = rihv_autotune
 
     # -- profiling ----------------------------------------------------------
+    def rihv_selftest_bounded_wait(self, polls=4096):
+        """Runs the library's bounded mbarrier wait on a barrier nothing
+        arrives on; returns the status code without raising (5,
+        RIHV_ERR_TIMEOUT, is the expected outcome)."""
+        return self.L.rihv_selftest_bounded_wait(self.h, int(polls))
+
     def set_profiling(self, on):
         """False/0 off; True/1 stage events; 2 also events around every TV launch."""
         self._check(self.L.rihv_set_profiling(self.h, int(on)), self.h)
