@@ -131,15 +131,25 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _code_lines(path):
+    """The lines of a C++ source with // comments and blank lines removed."""
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            yield code
+
+
 def kernel_hash():
-    """Hash of the TV kernel source and of the TV lines of the internal header,
-    so that the committed DRAM traffic is used only for the kernel it measured."""
+    """Hash of the TV kernel source and of the TV lines of the internal header
+    (code only: comments do not count), so that the committed DRAM traffic is
+    used only for the kernel it measured."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1904_04884_gb300", "csrc")
-    h.update(open(os.path.join(csrc, "tv_kernels.cu"), "rb").read())
-    for line in open(os.path.join(csrc, "rihv_internal.cuh"), "rb"):
-        if b"Tv" in line or b"TV" in line or b"tv_" in line:
-            h.update(line)
+    for line in _code_lines(os.path.join(csrc, "tv_kernels.cu")):
+        h.update(line.encode() + b"\n")
+    for line in _code_lines(os.path.join(csrc, "rihv_internal.cuh")):
+        if "Tv" in line or "TV" in line or "tv_" in line:
+            h.update(line.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

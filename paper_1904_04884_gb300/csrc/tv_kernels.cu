@@ -8,22 +8,28 @@
 // where (D_x^H p)_i = p_{i-1} [i >= 1] - p_i [i <= n-2] (same along y and z)
 // and Pi scales the voxel's (p_x, p_y, p_z) in C^3 onto the unit ball.
 //
-// The TV kernels march a 32x8 x-y tile through a chunk of planes (2.5D
+// The TV kernels stream an x-y tile through a chunk of planes (2.5D
 // blocking). Each plane of v, p_x, p_y, p_z arrives in shared memory as one
-// TMA box (x from i0-2, y from j0-1 for one step or j0-2 for two: the
-// stencil's halo, with the x start kept on a 16-byte boundary; out-of-range
-// boxes are zero filled) into a 4-stage ring completed by mbarriers, so two planes are in flight while one is
-// computed. k_tv_step2 performs two dual steps per launch (temporal blocking,
-// first step recomputed on a one-voxel halo ring, one warp per tile row);
-// k_tv_step performs one (for odd step counts). Outputs go out with plain coalesced stores. Every
-// wait is bounded: on timeout the CTA sets the error flag, drains its copies
-// in flight and exits.
+// TMA box (the stencil's halo included, its x start kept on a 16-byte
+// boundary; out-of-range boxes are zero filled) in a ring of stages completed
+// by mbarriers, so that planes are in flight while one is computed.
+//   k_tv_step:  one dual step, 32 x 8 tile, one thread per position, 4 stages.
+//   k_tv_step2: two dual steps per launch (temporal blocking: the first step
+//               recomputed on a one-voxel halo ring), one warp per tile row,
+//               two x positions per lane, 60 x 16 tile, 3 stages. Its FINAL
+//               form (58 x 11 tile, one more halo ring) also forms
+//               x = soft(v - mu D^H p^2) and, for FISTA, y_{k+1} and the
+//               restart product, so the last dual field never reaches memory.
+// An odd step count starts with one k_tv_step launch. Outputs go out with
+// plain coalesced stores. Every wait is bounded: on timeout the CTA sets the
+// error flag, drains its copies in flight (bounded) and exits.
 //
-// The finalize kernel forms u = v - mu D^H p, soft-thresholds it, and (in
-// FISTA mode) writes x_k and y_{k+1} = x_k + beta (x_k - x_{k-1}) and reduces
-// the gradient-restart inner product Re<y_k - x_k, x_k - x_{k-1}> in FP64.
-// The last block of the grid (ticket counter) updates t, beta and the restart
-// flag on the device, so no scalar crosses to the host.
+// The separate finalize kernel (used when the finalize is not fused) forms
+// u = v - mu D^H p, soft-thresholds it, and in FISTA mode writes x_k and
+// y_{k+1} = x_k + beta (x_k - x_{k-1}) and reduces the gradient-restart
+// inner product Re<y_k - x_k, x_k - x_{k-1}> (FP32 over 8 voxels, FP64
+// above). The last block of the grid (ticket counter) updates t, beta and the
+// restart flag on the device, so no scalar crosses to the host.
 #include <cuda_runtime.h>
 
 #include "rihv_internal.cuh"
