@@ -966,22 +966,26 @@ int stream_grid(size_t nvox) {
 
 int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final) {
   if (nsteps != 2) return 32;
-  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks. Pick the
-  // chunk that minimises (waves, rounded up) x (ticks per chunk).
+  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks (zc + 4 for
+  // the fused final launch, one more plane of z halo). The cost of a chunk
+  // size is (waves, rounded up) x (ticks per chunk), over chunks in [8, 256].
+  // Every chunk also reads its z halo again, which this count leaves out, so
+  // among the chunks within 3 % of the lowest cost the largest is taken.
   const int tx = final ? kTv2TxF : TX2, ty = final ? kTv2TyF : kTv2Ty;
+  const int halo = final ? 4 : 3;
   const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
-  int best = 32;
-  long best_cost = -1;
-  for (int zc : {16, 32, 64, 128, 256}) {
-    const int c = zc < nz ? zc : nz;
+  auto cost = [&](int c) {
     const long ctas = tiles * ((nz + c - 1) / c);
-    const long cost = ((ctas + sms - 1) / sms) * (c + 3);
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best = c;
-    }
-    if (c == nz) break;
-  }
+    return ((ctas + sms - 1) / sms) * (c + halo);
+  };
+  const int cmax = nz < kTvMaxChunk ? nz : kTvMaxChunk;
+  const int cmin = nz < 8 ? nz : 8;
+  long lowest = -1;
+  for (int c = cmin; c <= cmax; ++c)
+    if (lowest < 0 || cost(c) < lowest) lowest = cost(c);
+  int best = cmin;
+  for (int c = cmin; c <= cmax; ++c)
+    if (cost(c) * 100 <= lowest * 103) best = c;
   return best;
 }
 

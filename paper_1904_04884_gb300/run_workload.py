@@ -41,7 +41,7 @@ def match(parts, discs, tol_xy, tol_z):
 
 
 def run(name, tv_dims=None, iters=None, lam_l1=None, lam_tv=None, tol_xy=2.0, tol_z=5.0,
-        n_inner=None, skip_empty_planes=1):
+        n_inner=None, skip_empty_planes=0):
     w = workloads.ALL[name]
     dev = torch.device("cuda:0")
     h = Rihv(*w.optics_tuple())
@@ -106,7 +106,7 @@ def main():
     p.add_argument("--match-xy", type=float, default=2.0)
     p.add_argument("--match-z", type=float, default=5.0)
     p.add_argument("--n-inner", type=int, default=None)
-    p.add_argument("--skip-empty-planes", type=int, default=1, choices=[0, 1])
+    p.add_argument("--skip-empty-planes", type=int, default=0, choices=[0, 1])
     a = p.parse_args()
     run(a.workload, a.tv_dims, a.iters, a.lam_l1, a.lam_tv, a.match_xy, a.match_z, a.n_inner,
         a.skip_empty_planes)
