@@ -258,12 +258,17 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_rows(const __grid_constant__
 // accumulation); the angle in [-pi, pi) goes to the hardware sine/cosine
 // approximation (absolute error about 5e-7 on this range), well inside the
 // operators' 1e-5 relative budget and far cheaper than the accurate routine.
-__device__ __forceinline__ float2 transfer(uint2 ph, float amp, int j) {
+__device__ __forceinline__ float2 phase_rot(uint2 ph, int j) {
   const unsigned phi = ph.x + static_cast<unsigned>(j) * ph.y;   // wraps modulo 1 cycle
   const float half_cycles = static_cast<float>(static_cast<int>(phi)) * 4.656612873077393e-10f;  // 2^-31
   float s, c;
   __sincosf(half_cycles * 3.14159265358979f, &s, &c);
-  return make_float2(amp * c, amp * s);
+  return make_float2(c, s);
+}
+// H_j at one frequency: the band mask (exactly 0 or 1) times the rotation.
+__device__ __forceinline__ float2 transfer(uint2 ph, float amp, int j) {
+  const float2 r = phase_rot(ph, j);
+  return make_float2(amp * r.x, amp * r.y);
 }
 
 template <int MODE>
@@ -572,15 +577,12 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
   if (MODE == COL_FWD_ZSUM || MODE == COL_ADJ_GEN) {
     const int z0 = blockIdx.y * a.z_per_group;
     const int z1 = min(a.nz, z0 + a.z_per_group);
-    // transfer-function phases and band mask of this thread's frequencies
+    // transfer-function phases of this thread's frequencies; the band mask
+    // (exactly 0 or 1, the same for every plane) is applied once, outside the
+    // plane loop: to the z-sum in the forward, to R in the adjoint
     uint2 ph[8];
-    float amp[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const size_t o = s * strip_elems + (i + TT * e) * W + w;
-      ph[e] = __ldg(a.phase + o);
-      amp[e] = __ldg(a.amp + o);
-    }
+    for (int e = 0; e < 8; ++e) ph[e] = __ldg(a.phase + s * strip_elems + (i + TT * e) * W + w);
     if (MODE == COL_FWD_ZSUM) {
       float2 acc[8];
 #pragma unroll
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
           }
           rfft<N, false>(v, i, xa, xb, tw);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(phase_rot(ph[e], z), v[e]));
         }
       } else {
         auto next_live = [&](int z) {
@@ -632,23 +634,27 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
           }
           rfft<N, false>(v, i, xa, xb, tw);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(transfer(ph[e], amp[e], z), v[e]));
+          for (int e = 0; e < 8; ++e) acc[e] = cadd(acc[e], cmul(phase_rot(ph[e], z), v[e]));
           z = zn;
         }
       }
       float2* dst = a.dst + static_cast<size_t>(blockIdx.y) * a.nx * a.ny;
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        dst[static_cast<size_t>(i + TT * e) * a.nx + s * W + w] = acc[e];
+      for (int e = 0; e < 8; ++e) {
+        const float amp = __ldg(a.amp + s * strip_elems + (i + TT * e) * W + w);
+        dst[static_cast<size_t>(i + TT * e) * a.nx + s * W + w] = cscale(acc[e], amp);
+      }
     } else {
       float2 rr[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        rr[e] = cscale(a.src[static_cast<size_t>(i + TT * e) * a.nx + s * W + w], a.scale);
+      for (int e = 0; e < 8; ++e) {
+        const float amp = __ldg(a.amp + s * strip_elems + (i + TT * e) * W + w);
+        rr[e] = cscale(cscale(a.src[static_cast<size_t>(i + TT * e) * a.nx + s * W + w], a.scale), amp);
+      }
       for (int z = z0; z < z1; ++z) {
         float2 v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = cmulc(rr[e], transfer(ph[e], amp[e], z));
+        for (int e = 0; e < 8; ++e) v[e] = cmulc(rr[e], phase_rot(ph[e], z));
         rfft<N, true>(v, i, xa, xb, tw);
         float2* dst = a.dst + (static_cast<size_t>(z) * nstrip + s) * strip_elems;
 #pragma unroll
