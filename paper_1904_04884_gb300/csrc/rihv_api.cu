@@ -303,6 +303,39 @@ rihv_status fft2_plane(rihv_ctx* h, const void* src, bool real_in, float2* out) 
   return RIHV_OK;
 }
 
+// TV launch geometry (host policy; the kernels take the chunk as an argument).
+// CTAs of a fused-final TV launch for a z-chunk.
+int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
+  return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
+}
+
+// Planes per z-chunk of a TV launch when none was tuned (final: the
+// fused-finalize launch's tile).
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false) {
+  if (nsteps != 2) return 32;
+  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks (zc + 4 for
+  // the fused final launch, one more plane of z halo). The cost of a chunk
+  // size is (waves, rounded up) x (ticks per chunk), over chunks in [8, 256].
+  // Every chunk also reads its z halo again, which this count leaves out, so
+  // among the chunks within 3 % of the lowest cost the largest is taken.
+  const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
+  const int halo = final ? 4 : 3;
+  const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+  auto cost = [&](int c) {
+    const long ctas = tiles * ((nz + c - 1) / c);
+    return ((ctas + sms - 1) / sms) * (c + halo);
+  };
+  const int cmax = nz < kTvMaxChunk ? nz : kTvMaxChunk;
+  const int cmin = nz < 8 ? nz : 8;
+  long lowest = -1;
+  for (int c = cmin; c <= cmax; ++c)
+    if (lowest < 0 || cost(c) < lowest) lowest = cost(c);
+  int best = cmin;
+  for (int c = cmin; c <= cmax; ++c)
+    if (cost(c) * 100 <= lowest * 103) best = c;
+  return best;
+}
+
 // K dual steps; returns the buffer set holding the final p. With `fin` (two
 // steps per launch, K >= 2) the last launch also runs the finalize and
 // *pfinal is null.

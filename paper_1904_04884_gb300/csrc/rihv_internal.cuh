@@ -158,11 +158,6 @@ struct TvArgs {
 // final (two-step launches only): fused finalize, no dual output.
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s,
                            bool final = false);
-// CTAs of a fused-finalize launch (sizes fin_partials).
-int tv_final_ctas(int nx, int ny, int nz, int zchunk);
-// Planes per z-chunk of the TV launch grid when none was tuned (final: the
-// fused-finalize launch's tile).
-int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false);
 // Box of box_rows x box_cols complex elements: (kTvBoxH1, kTvBoxW) for the
 // one-step kernel, (kTv2BoxH, kTv2BoxW) for the two-step kernel.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,

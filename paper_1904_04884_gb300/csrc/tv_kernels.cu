@@ -964,31 +964,6 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
-int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final) {
-  if (nsteps != 2) return 32;
-  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks (zc + 4 for
-  // the fused final launch, one more plane of z halo). The cost of a chunk
-  // size is (waves, rounded up) x (ticks per chunk), over chunks in [8, 256].
-  // Every chunk also reads its z halo again, which this count leaves out, so
-  // among the chunks within 3 % of the lowest cost the largest is taken.
-  const int tx = final ? kTv2TxF : TX2, ty = final ? kTv2TyF : kTv2Ty;
-  const int halo = final ? 4 : 3;
-  const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
-  auto cost = [&](int c) {
-    const long ctas = tiles * ((nz + c - 1) / c);
-    return ((ctas + sms - 1) / sms) * (c + halo);
-  };
-  const int cmax = nz < kTvMaxChunk ? nz : kTvMaxChunk;
-  const int cmin = nz < 8 ? nz : 8;
-  long lowest = -1;
-  for (int c = cmin; c <= cmax; ++c)
-    if (lowest < 0 || cost(c) < lowest) lowest = cost(c);
-  int best = cmin;
-  for (int c = cmin; c <= cmax; ++c)
-    if (cost(c) * 100 <= lowest * 103) best = c;
-  return best;
-}
-
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s, bool final) {
   if (nsteps == 2 && (a.nx & 1)) return cudaErrorInvalidValue;   // pairs of x positions
   if (final && nsteps != 2) return cudaErrorInvalidValue;
@@ -1013,9 +988,6 @@ cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t
   return cudaGetLastError();
 }
 
-int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
-  return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
-}
 
 cudaError_t encode_tmap(CUtensorMap* tm, CUtensorMapDataType type, int rank, const void* base,
                         const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
