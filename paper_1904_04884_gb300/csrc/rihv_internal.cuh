@@ -237,6 +237,9 @@ constexpr int kConvTW = 128;                   // output voxels along x per CTA 
 constexpr int kConvTH = 2;                     // output rows (y) per CTA
 constexpr int kConvHX = kConvTW + 2;           // halo width
 constexpr int kConvHaloKu = 3 * (kConvTH + 2) * kConvHX * 16;   // bytes per 8-channel group
+// each group's box is a TMA tile copy, whose shared-memory destination must
+// sit on a 128-byte boundary (with 4 rows per CTA, 37,440 B, it would not)
+static_assert(kConvHaloKu % 128 == 0, "conv halo boxes must start on 128-byte boundaries");
 constexpr int kConvHaloBytes = 2 * kConvHaloKu;                 // 16 channels
 constexpr int kConvMaxGroups = 32;             // 256 channels / 8
 struct ConvMaps {
