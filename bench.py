@@ -27,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -92,7 +93,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples: RIHV_CLOCKS_DIR if set, else the system's temporary directory
+        out_dir = os.environ.get("RIHV_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"rihv_clocks_rank{index}.csv")
 
     def start(self):
         try:

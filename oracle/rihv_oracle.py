@@ -14,7 +14,7 @@ component labelling (``scipy.ndimage.label``).
 Paper: "Regularized Inverse Holographic Volume Reconstruction for 3D Particle
 Tracking" (arXiv 1904.04884), Section 2 (Methodology).
 
-Readings where the paper is silent or garbled (each is also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 R1  Grid and frequencies. Pixel (i, j), i fastest along x. Frequencies in FFT
     order, f_x = k_x / (n_x * pitch). Planes z_j = z0 + j*dz. (Section 2 gives no

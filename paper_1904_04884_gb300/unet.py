@@ -5,7 +5,7 @@ channels: real and imaginary part) of one volume to an initial volume for the
 fused-lasso FISTA solve, x0 = base_coeff * H^H b + scale_out * net(H^H b): the
 first term is FISTA's own first iterate from zero (base_coeff = 2 tau), so the
 network learns the correction that FISTA would otherwise build over many
-iterations. Plain FISTA from zero remains the fallback and the judge of the
+iterations. Plain FISTA from zero remains the fallback and the reference for the
 result (the solver refines x0 to the same objective).
 
 Architecture (3 levels, 16/32/64 channels, 3x3x3 convolutions, BF16 weights
