@@ -736,6 +736,53 @@ __global__ void __launch_bounds__(kRedThreads) k_zsum(const float2* partial, int
   }
 }
 
+// The forward of the iterate x_k, summed over z-groups, feeds both the
+// objective (data term of x_k) and the next gradient: the residual spectrum of
+// y_{k+1} = x_k + beta (x_k - x_{k-1}) follows by linearity from S(x_k) and
+// S(x_{k-1}), so y never needs a forward of its own.
+__global__ void __launch_bounds__(kRedThreads) k_zsum_next(const float2* partial, int groups,
+                                                           const float2* bhat,
+                                                           const float2* sx_prev, float2* sx,
+                                                           float2* ry, int nxy, double inv_nxy,
+                                                           DevScalars* sc, RedWork w) {
+  const float beta = sc->restart_flag ? 0.f : static_cast<float>(sc->beta_used);
+  double local = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nxy; idx += gridDim.x * blockDim.x) {
+    float2 acc = partial[idx];
+    for (int g = 1; g < groups; ++g) acc = cadd(acc, partial[static_cast<size_t>(g) * nxy + idx]);
+    sx[idx] = acc;
+    const float2 b = bhat[idx];
+    const float2 r = csub(acc, b);
+    local += static_cast<double>(r.x * r.x + r.y * r.y);
+    float2 yv = acc;
+    if (beta != 0.f) {
+      const float2 p = sx_prev[idx];
+      yv = make_float2(acc.x + beta * (acc.x - p.x), acc.y + beta * (acc.y - p.y));
+    }
+    ry[idx] = csub(yv, b);
+  }
+  const double bs = block_sum(local);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    w.partials[blockIdx.x] = bs;
+    __threadfence();
+    last = atomicAdd(&w.tickets[0], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
+    v += static_cast<volatile double*>(w.partials)[b];
+  const double tot = block_sum(v);
+  if (threadIdx.x == 0) {
+    const double r2 = tot * inv_nxy;
+    sc->rnorm2 = r2;
+    if (!isfinite(r2)) sc->nonfinite = 1;
+    w.tickets[0] = 0;
+  }
+}
+
 template <bool INV, int IN, int OUT, int EPI, int N>
 cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
   using Sh = RShape<N>;
@@ -869,6 +916,17 @@ cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, f
   int blocks = (nxy + kRedThreads - 1) / kRedThreads;
   if (blocks > kRedBlocks) blocks = kRedBlocks;
   k_zsum<<<blocks, kRedThreads, 0, s>>>(partial, groups, bhat, out, nxy, 1.0 / nxy, sc, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zsum_next(const float2* partial, int groups, const float2* bhat,
+                             const float2* sx_prev, float2* sx, float2* ry, int nx, int ny,
+                             DevScalars* sc, RedWork w, cudaStream_t s) {
+  const int nxy = nx * ny;
+  int blocks = (nxy + kRedThreads - 1) / kRedThreads;
+  if (blocks > kRedBlocks) blocks = kRedBlocks;
+  k_zsum_next<<<blocks, kRedThreads, 0, s>>>(partial, groups, bhat, sx_prev, sx, ry, nxy,
+                                             1.0 / nxy, sc, w);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ struct rihv_ctx {
   float2* inter = nullptr;     // strip-major intermediate [nz][nx/W][ny][W]
   float2* partial = nullptr;   // [groups][ny][nx]
   float2* spec = nullptr;      // [ny][nx] spectrum sum / residual spectrum
+  float2* sx[2] = {nullptr, nullptr};   // [ny][nx] F H x_k of the last two iterates
   float2* bhat = nullptr;      // [ny][nx] F b
   float* holo = nullptr;       // [ny][nx]
   float2* x = nullptr;         // volumes
@@ -279,6 +280,24 @@ rihv_status forward_spectrum(rihv_ctx* h, const float2* xin, const float2* bhat,
   CK(launch_rows(0, ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE, ra, h->stream));
   CK(launch_cols(COL_FWD_ZSUM, ca, h->groups, h->stream));
   CK(launch_zsum(h->partial, h->groups, bhat, out, h->nx, h->ny, h->sc, h->red, h->stream));
+  return RIHV_OK;
+}
+
+// Forward of the iterate x_k (k = 0: x_0, in the set-up): F H x_k -> sx[k & 1],
+// its data term ||H x_k - b||^2 -> sc->rnorm2, and the residual spectrum of
+// y_{k+1} -> spec by linearity from F H x_k and F H x_{k-1} (the momentum and
+// restart the finalize of iteration k applied). With occ, all-zero planes
+// of x_k are skipped.
+rihv_status forward_iterate(rihv_ctx* h, const float2* xin, int k, const int* occ) {
+  StageScope sc(h, ST_FORWARD, 3);
+  RowArgs ra = row_args(h, xin, h->inter, h->nz);
+  ColArgs ca = col_args(h, h->inter, h->partial);
+  ra.occ = occ;
+  ca.occ = occ;
+  CK(launch_rows(0, ROW_IN_C64, ROW_OUT_STRIP, ROW_EPI_SCALE, ra, h->stream));
+  CK(launch_cols(COL_FWD_ZSUM, ca, h->groups, h->stream));
+  CK(launch_zsum_next(h->partial, h->groups, h->bhat, h->sx[(k + 1) & 1], h->sx[k & 1], h->spec,
+                      h->nx, h->ny, h->sc, h->red, h->stream));
   return RIHV_OK;
 }
 
@@ -491,8 +510,6 @@ rihv_status ensure_trace(rihv_ctx* h, int nchecks) {
   return RIHV_OK;
 }
 
-// Solve set-up from the hologram already in h->holo: F b, x_0 (zero unless
-// warm, in which case h->x already holds it), y_1 = x_0, scalars, flags.
 // End of a chunk of FISTA iterations inside a batched graph: records the
 // iterations run and, if a chunk follows, sets its IF condition: stop once
 // the objective just computed is <= the threshold (rihv_solve's test).
@@ -511,38 +528,42 @@ cudaError_t launch_chunk_end(int* done, int k_end, const double* f, double thr,
   return cudaGetLastError();
 }
 
+// Solve set-up from the hologram already in h->holo: F b, x_0 (zero unless
+// warm, in which case h->x already holds it), y_1 = x_0, scalars, flags, and
+// the forward of x_0.
 rihv_status enqueue_setup(rihv_ctx* h, bool warm) {
   StageScope sc(h, ST_SETUP, 3);
   CKS(fft2_plane(h, h->holo, true, h->bhat));
   const size_t vb = h->nvox * sizeof(float2);
   if (!warm) CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
   CK(cudaMemcpyAsync(h->y, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
-  // occupancy of y_1 = x_0: no plane from zero, every plane from a warm
-  // start; occ[nz] = some plane empty
-  CK(cudaMemsetAsync(h->occ, warm ? 1 : 0, sizeof(int) * h->nz, h->stream));
-  CK(cudaMemsetAsync(h->occ + h->nz, warm ? 0 : 1, sizeof(int), h->stream));
   CK(launch_init_scalars(h->sc, h->opt.accelerate, h->opt.restart, h->stream));
   CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
+  // F H x_0, and the residual spectrum of y_1 = x_0
+  CKS(forward_iterate(h, h->x, 0, nullptr));
   return RIHV_OK;
 }
 
-// FISTA iteration k (1-based): forward and residual spectrum, gradient step,
-// fused-lasso prox with momentum and restart; every check_every iterations the
-// objective F(x_k) goes to trace slot *check, which is then incremented.
+// FISTA iteration k (1-based): gradient step from the residual spectrum of
+// y_k, fused-lasso prox with momentum and restart, then the forward of x_k
+// (one forward per iteration: it gives F(x_k)'s data term and, by linearity,
+// the residual of y_{k+1}); every check_every iterations the objective F(x_k)
+// goes to trace slot *check, which is then incremented.
 rihv_status enqueue_iteration(rihv_ctx* h, int k, float lambda_l1, float lambda_tv, int* check) {
   const float tau = static_cast<float>(h->tau);
   const float grad_scale = static_cast<float>(2.0 * h->tau / static_cast<double>(h->nxy));
-  // planes of y_k (and of x_k below) that are all zero skip the forward
-  const int* occ = occ_tracked(h, tau * lambda_tv) ? h->occ : nullptr;
-  // (a) forward and residual spectrum R = F(H y - b)
-  CKS(forward_spectrum(h, h->y, h->bhat, h->spec, occ));
-  // (c) v = y - tau * 2 H^H r
+  // (c) v = y - tau * 2 H^H r, with R = F(H y_k - b) in spec (left there by
+  // the forward of the previous iterate, or by the set-up)
   CKS(adjoint_planes(h, h->spec, h->y, h->v, grad_scale, true));
   // (d) x_k = prox(v), momentum, restart
   CKS(prox_into(h, h->v, tau * lambda_l1, tau * lambda_tv, h->opt.n_inner, FIN_FISTA, h->x));
+  // (a) forward of x_k: the data term of F(x_k) and R = F(H y_{k+1} - b) for
+  // the next iteration; with the empty-plane skip, all-zero planes of x_k
+  // are left out
+  const int* occ = occ_tracked(h, tau * lambda_tv) ? h->occ : nullptr;
+  CKS(forward_iterate(h, h->x, k, occ));
   const int M = h->opt.check_every;
   if (M > 0 && k % M == 0) {
-    CKS(forward_spectrum(h, h->x, h->bhat, h->spec, occ));
     StageScope sc(h, ST_OBJECTIVE, 1);
     CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, lambda_l1, lambda_tv, h->sc,
                         h->red, h->trace + *check, h->stream));
@@ -630,6 +651,8 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   AL(h->inter, h->nvox);
   AL(h->partial, h->nxy * kMaxGroups);
   AL(h->spec, h->nxy);
+  AL(h->sx[0], h->nxy);
+  AL(h->sx[1], h->nxy);
   AL(h->bhat, h->nxy);
   AL(h->holo, h->nxy);
   AL(h->x, h->nvox);

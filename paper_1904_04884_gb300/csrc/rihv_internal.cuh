@@ -60,6 +60,7 @@ struct FftPlan {
 struct DevScalars {
   double t;            // FISTA t_k
   double beta;         // momentum factor of the current iteration
+  double beta_used;    // the factor the last finalize applied to form y_{k+1}
   double restart_dot;  // Re<y_k - x_k, x_k - x_{k-1}> of the last iteration
   double rnorm2;       // ||H x - b||^2 of the last forward with a hologram
   double l1;           // ||x||_1 of the last objective evaluation
@@ -124,6 +125,14 @@ int cols_ctas_per_sm(int ny);
 // S = sum_g partial[g]; if bhat: out = S - bhat and ||out||^2 / (nx ny) -> sc->rnorm2.
 cudaError_t launch_zsum(const float2* partial, int groups, const float2* bhat, float2* out,
                         int nx, int ny, DevScalars* sc, RedWork w, cudaStream_t s);
+// After the forward of the iterate x_k (partials of its z-groups): S_x = F H x_k
+// -> sx; ||S_x - F b||^2 / (nx ny) -> sc->rnorm2 (the data term of x_k); and, by
+// linearity, the residual spectrum of y_{k+1} = x_k + beta (x_k - x_{k-1}) ->
+// ry: S_x + beta (S_x - sx_prev) - F b with the beta the finalize used
+// (sc->beta_used), or S_x - F b after a restart (sc->restart_flag).
+cudaError_t launch_zsum_next(const float2* partial, int groups, const float2* bhat,
+                             const float2* sx_prev, float2* sx, float2* ry, int nx, int ny,
+                             DevScalars* sc, RedWork w, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // TV / prox / FISTA kernels (tv_kernels.cu)

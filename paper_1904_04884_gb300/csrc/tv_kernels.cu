@@ -339,6 +339,7 @@ __device__ __forceinline__ float2 soft(float2 u, float kappa) {
 // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, or 1 on restart; beta for the next
 // extrapolation from t_{k+1} and t_{k+2}.
 __device__ __forceinline__ void fista_update(DevScalars* sc, double dot) {
+  sc->beta_used = sc->beta;
   sc->restart_dot = dot;
   if (!isfinite(dot)) sc->nonfinite = 1;
   double t = sc->t;
@@ -947,6 +948,7 @@ __global__ void __launch_bounds__(kRedThreads) k_objective(const float2* x, int 
 __global__ void k_init_scalars(DevScalars* sc, int accelerate, int restart) {
   sc->t = 1.0;
   sc->beta = 0.0;  // (t_1 - 1) / t_2 with t_1 = 1
+  sc->beta_used = 0.0;
   sc->restart_dot = 0.0;
   sc->rnorm2 = 0.0;
   sc->l1 = 0.0;
