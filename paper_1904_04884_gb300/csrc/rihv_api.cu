@@ -75,6 +75,7 @@ struct rihv_ctx {
   int groups = 1, zpg = 1;
   int sms = 152;
   int tv_zchunk = 0;                 // planes per TV z-chunk; 0: tv_default_zchunk
+  bool batch_chunks = false;         // being captured into a batched graph (see tv_steps)
   double* fin_partials = nullptr;    // one per CTA of a fused-finalize TV launch
   int fin_ctas = 0;                  // capacity of fin_partials
   double tau = 0;
@@ -376,7 +377,15 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   a.ny = h->ny;
   a.nz = h->nz;
   a.dims = h->opt.tv_dims;
-  const int zc_auto = tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
+  // In a batched graph the branches run concurrently, so the two-step
+  // launches take the largest chunk (fewest halo planes read twice) rather
+  // than the one that fills the waves of a lone launch. The fused-final
+  // launch keeps the lone-solve chunk: its restart-product partials follow
+  // the chunking, and with them a batched solve stays bitwise equal to a
+  // single one (no other TV result depends on the chunk).
+  const int zc_auto = (h->batch_chunks && per == 2)
+                          ? std::min(h->nz, kTvMaxChunk)
+                          : tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
   const int zc_final = tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true);
   a.mu = mu;
   a.step = 1.f / (4.f * a.dims * mu);
@@ -1146,8 +1155,12 @@ static rihv_status batch_capture_cond(rihv_batch b, float l1, float ltv, int ite
     cudaGraph_t g = nullptr;
     cudaGraphNode_t prev = nullptr, node = nullptr;
     int check = 0;
+    h->batch_chunks = true;
     st = capture_graph(h, b->branch[i], &g, [&] { return enqueue_setup(h, warm); });
-    if (st != RIHV_OK) break;
+    if (st != RIHV_OK) {
+      h->batch_chunks = false;
+      break;
+    }
     e = add_child(root, g, nullptr, &node);
     prev = node;
     const int chunk = stop ? M : iters;
@@ -1186,6 +1199,7 @@ static rihv_status batch_capture_cond(rihv_batch b, float l1, float ltv, int ite
       }
       prev = node;
     }
+    h->batch_chunks = false;
     b->checks[i] = check;
     for (int s = 0; s < kNumStages; ++s) {
       b->launches[i][s] = h->stage_launches[s] - before[s];
@@ -1239,9 +1253,11 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     long long before[kNumStages];
     for (int s = 0; s < kNumStages; ++s) before[s] = h->stage_launches[s];
     cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    h->batch_chunks = true;
     st = enqueue_setup(h, warm);
     int check = 0;
     for (int k = 1; k <= iters && st == RIHV_OK; ++k) st = enqueue_iteration(h, k, l1, ltv, &check);
+    h->batch_chunks = false;
     b->checks[i] = check;
     for (int s = 0; s < kNumStages; ++s) {
       b->launches[i][s] = h->stage_launches[s] - before[s];
