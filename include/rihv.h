@@ -21,8 +21,9 @@
  *    b <= 1}; 1 <= nz <= 4096. Other sizes return RIHV_ERR_UNSUPPORTED_SIZE.
  *  - Pointers marked "device" must be CUDA device memory of the current
  *    device, 16-byte aligned and not overlapping each other. Pointers marked
- *    "host or device" may also be host memory; the library then copies
- *    through its own staging buffers (the call synchronises the stream).
+ *    "host or device" may also be host memory (pinned or pageable); the
+ *    library copies it with cudaMemcpyAsync on the handle's stream into or
+ *    out of its own device buffers, and the call synchronises the stream.
  *  - All work is queued on the handle's stream (rihv_set_stream; default: the
  *    legacy default stream). Calls return once the work is queued unless they
  *    say otherwise. The caller owns every pointer it passes; the library owns
