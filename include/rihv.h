@@ -183,8 +183,10 @@ rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_
  * complex64 output volume; traces: NULL or per-handle host or device arrays
  * of iters / check_every doubles (NULL entries allowed). Handles whose
  * options set a stop test stop early inside the graph (see
- * rihv_batch_iterations); the others run `iters`. The call returns after the
- * batch has finished. */
+ * rihv_batch_iterations); the others run `iters`. Each handle's volume and
+ * trace are bitwise equal to those of its own rihv_solve (inside the graph the
+ * TV launches before the last one of each prox run on larger z-chunks, which
+ * changes no result). The call returns after the batch has finished. */
 typedef struct rihv_batch_st* rihv_batch;
 rihv_status rihv_batch_create(const rihv_handle* handles, int n, rihv_batch* out);
 rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float lambda_l1,
