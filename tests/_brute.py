@@ -139,3 +139,37 @@ def flood_fill_components(mask):
                                     q.append((aa, bb, cc))
                 comps.append(sorted(members))
     return comps
+
+
+def fista_three_sequence(grad, prox, tau, x0, iters, restart=False):
+    """Accelerated proximal gradient in the three-sequence form (Tseng 2008,
+    the form Nesterov's method is often stated in), written independently of
+    the oracle's FISTA driver. With t_1 = 1, for k = 1, 2, ...:
+
+        x_k     = prox(y_k - tau grad(y_k))
+        z_k     = x_{k-1} + t_k (x_k - x_{k-1})
+        t_{k+1} = the positive root of t^2 - t - t_k^2 = 0
+        y_{k+1} = (1 - 1/t_{k+1}) x_k + z_k / t_{k+1}
+
+    Expanding y_{k+1} gives Beck and Teboulle's x_k + ((t_k - 1)/t_{k+1})
+    (x_k - x_{k-1}), so the iterates agree with FISTA to rounding, but every
+    quantity is computed differently. With ``restart`` the gradient restart of
+    O'Donoghue and Candes applies: when Re<y_k - x_k, x_k - x_{k-1}> > 0 the
+    sequence starts over, t_{k+1} = 1 and y_{k+1} = x_k. ``grad`` and ``prox``
+    are callables. Returns the list of iterates x_1 ... x_iters."""
+    x_prev = np.array(x0, dtype=np.complex128)
+    y = x_prev.copy()
+    t = 1.0
+    xs = []
+    for _ in range(iters):
+        x = prox(y - tau * grad(y))
+        if restart and np.sum(((y - x).conj() * (x - x_prev)).real) > 0.0:
+            t, y = 1.0, x.copy()
+        else:
+            z = x_prev + t * (x - x_prev)
+            roots = np.roots([1.0, -1.0, -t * t])
+            t = float(np.max(roots.real))
+            y = (1.0 - 1.0 / t) * x + z / t
+        x_prev = x
+        xs.append(x)
+    return xs

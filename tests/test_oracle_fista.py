@@ -101,3 +101,71 @@ def test_objective_trace_and_warm_start():
     xl, _ = O.fista(b, SMALL, 0.2, 0.0, iters=3000, n_inner=0)
     xw, _ = O.fista(b, SMALL, 0.2, 0.0, iters=5, n_inner=0, x0=xl)
     assert np.linalg.norm(xw - xl) < 1e-6 * np.linalg.norm(xl)
+
+
+@pytest.mark.parametrize("restart", [False, True])
+def test_fista_iterates_match_three_sequence_form(restart):
+    """The oracle's iterates x_1 ... x_20 equal those of an independent
+    three-sequence statement of the same accelerated method (tests/_brute.py)
+    to 1e-12, on a real operator with the TV term on. This pins the momentum
+    factor (t_k - 1)/t_{k+1} and the t recurrence: the pins above look at
+    converged or monotone behaviour only, where a wrong factor still passes.
+    The step, gradient and prox are the oracle's own, pinned elsewhere."""
+    b = _hologram(SMALL, 7)
+    lam1, lamtv, k_inner = 0.05, 0.08, 8
+    tau = 1.0 / O.lipschitz(SMALL)
+    xs = B.fista_three_sequence(lambda y: O.grad_data(y, b, SMALL),
+                                lambda v: O.prox_fused_lasso(v, tau * lam1, tau * lamtv, k_inner),
+                                tau, np.zeros(SMALL.shape), 20, restart=restart)
+    # the momentum must be doing something on this problem
+    assert np.linalg.norm(xs[2] - xs[1]) > 1e-6 * np.linalg.norm(xs[1])
+    for k in (1, 2, 3, 4, 6, 9, 14, 20):
+        x, _ = O.fista(b, SMALL, lam1, lamtv, iters=k, n_inner=k_inner, restart=restart)
+        ref = xs[k - 1]
+        assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref), k
+    # and a wrong factor t_k / t_{k+1} would not agree
+    ista, _ = O.fista(b, SMALL, lam1, lamtv, iters=3, n_inner=k_inner, accelerate=False)
+    assert np.linalg.norm(ista - xs[2]) > 1e-6 * np.linalg.norm(xs[2])
+
+
+def test_fista_iterates_by_hand():
+    """Three iterations written out by hand for an operator whose algebra is
+    plain: two planes both at z = 0 (nz = 2, z0 = dz = 0), so H x = x_0 + x_1,
+    L = 2 ||H||^2 = 4 and tau = 1/4, and the gradient step is
+    v_j = y_j - (y_0 + y_1 - b)/2 for both planes. With lam = 0 the first
+    iterate from the warm start (a, 0) is ((a + b)/2, (b - a)/2). With an L1
+    weight, x_k = soft_{tau lam}(v(y_k)), y_2 = x_1 (t_1 = 1) and
+    y_3 = x_2 + ((t_2 - 1)/t_3)(x_2 - x_1), t_2 = (1 + sqrt 5)/2: the third
+    iterate carries the momentum factor."""
+    op = O.Optics(nx=4, ny=2, nz=2, wavelength=632.8e-9, pitch=10e-6, z0=0.0, dz=0.0)
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((2, 4))
+    b = rng.standard_normal((2, 4))
+    x0 = np.stack([a, np.zeros_like(a)]).astype(complex)
+    x1, _ = O.fista(b, op, 0.0, 0.0, iters=1, n_inner=0, x0=x0)
+    np.testing.assert_allclose(x1[0], (a + b) / 2, atol=1e-14)
+    np.testing.assert_allclose(x1[1], (b - a) / 2, atol=1e-14)
+    # with lam > 0: x_k = soft_{tau lam}(v_k); three iterations by hand
+    lam = 0.4
+    k = lam / 4.0
+
+    def soft(u):
+        return np.sign(u) * np.maximum(np.abs(u) - k, 0.0)
+
+    def step(y):
+        r = y[0] + y[1] - b
+        return np.stack([soft(y[0] - r / 2), soft(y[1] - r / 2)])
+
+    t1 = 1.0
+    t2 = (1 + np.sqrt(5.0)) / 2
+    t3 = (1 + np.sqrt(1 + 4 * t2 * t2)) / 2
+    h1 = step(x0.real)
+    y2 = h1 + (t1 - 1) / t2 * (h1 - x0.real)
+    h2 = step(y2)
+    y3 = h2 + (t2 - 1) / t3 * (h2 - h1)
+    h3 = step(y3)
+    x3, _ = O.fista(b, op, lam, 0.0, iters=3, n_inner=0, x0=x0, restart=False)
+    np.testing.assert_allclose(x3.real, h3, atol=1e-13)
+    assert np.abs(x3.imag).max() == 0.0
+    # the momentum moved the third iterate
+    assert np.abs(step(h2) - h3).max() > 1e-3

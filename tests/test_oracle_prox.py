@@ -135,3 +135,58 @@ def test_gp_is_monotone_in_dual_objective():
         x = O.tv_prox_gp(v, mu, k)
         vals.append(np.vdot(x, x).real)
     assert all(b <= a + 1e-12 for a, b in zip(vals, vals[1:]))
+
+
+def _two_voxels(axis, a, c):
+    """A volume of two voxels along `axis` (0 = z, 1 = y, 2 = x) holding a, c."""
+    shape = [1, 1, 1]
+    shape[axis] = 2
+    v = np.zeros(shape, complex)
+    v.reshape(-1)[:] = [a, c]
+    return v
+
+
+@pytest.mark.parametrize("axis", [2, 1, 0])
+def test_gp_steps_by_hand(axis):
+    """Gradient projection on two voxels (0, 1) one apart, worked by hand.
+    From p = 0: u = v, D u = 1 on the first voxel and 0 on the last
+    (Neumann), so after one step p = step = 1/(4 dims mu) there, and
+    x = v - mu D^H p = (mu step, 1 - mu step) = (1/(4 dims), 1 - 1/(4 dims)):
+    (1/12, 11/12) in 3D, (1/8, 7/8) in 2D at mu = 1/2. A second 3D step:
+    u = (1/12, 11/12), D u = 10/12, p = 1/6 + (1/6)(10/12) = 11/36,
+    x = (11/72, 61/72). Along z the 2D prox (no z difference) returns v.
+    These fix the dual step constant 1/(4 dims mu), the sign and index of
+    D^H, and the order of the update."""
+    v = _two_voxels(axis, 0.0, 1.0)
+    mu = 0.5
+    x3 = O.tv_prox_gp(v, mu, 1, dims=3).reshape(-1)
+    np.testing.assert_allclose(x3, [1 / 12, 11 / 12], atol=1e-15)
+    x3b = O.tv_prox_gp(v, mu, 2, dims=3).reshape(-1)
+    np.testing.assert_allclose(x3b, [11 / 72, 61 / 72], atol=1e-15)
+    x2 = O.tv_prox_gp(v, mu, 1, dims=2).reshape(-1)
+    if axis == 0:
+        np.testing.assert_allclose(x2, [0.0, 1.0], atol=0)
+    else:
+        np.testing.assert_allclose(x2, [1 / 8, 7 / 8], atol=1e-15)
+    # complex values: the same numbers along the imaginary axis
+    xi = O.tv_prox_gp(_two_voxels(axis, 0.0, 1j), mu, 1, dims=3).reshape(-1)
+    np.testing.assert_allclose(xi, [1j / 12, 11j / 12], atol=1e-15)
+
+
+def test_gp_projection_by_hand():
+    """A jump of 10 at mu = 1/2: step * D u = 10/6 > 1, so the projection
+    clips p to 1 and x = (mu, 10 - mu) = (0.5, 9.5). With two components
+    (a jump of 3 along x and 4 along y from the corner voxel of a 2 x 2
+    plane), the corner's dual (3, 4)/6 has norm 5/6 < 1 and is kept; a jump
+    of (6, 8) gives (1, 4/3), norm 5/3, scaled back to (0.6, 0.8)."""
+    v = _two_voxels(2, 0.0, 10.0)
+    np.testing.assert_allclose(O.tv_prox_gp(v, 0.5, 1, 3).reshape(-1), [0.5, 9.5], atol=1e-14)
+    for jx, jy, pxy in ((3.0, 4.0, (0.5, 2 / 3)), (6.0, 8.0, (0.6, 0.8))):
+        w = np.zeros((1, 2, 2), complex)
+        w[0, 0, 1] = jx
+        w[0, 1, 0] = jy
+        x, (px, py, pz) = O.tv_prox_gp(w, 0.5, 1, 3, return_dual=True)
+        np.testing.assert_allclose([px[0, 0, 0].real, py[0, 0, 0].real], pxy, atol=1e-14)
+        # the corner has no backward neighbours: D^H p there is -(p_x + p_y)
+        dh00 = -(px[0, 0, 0] + py[0, 0, 0])
+        np.testing.assert_allclose(x[0, 0, 0], w[0, 0, 0] - 0.5 * dh00, atol=1e-14)
