@@ -242,10 +242,11 @@ rihv_status rihv_coo_expand(rihv_handle h, const long long* plane_offsets, const
                             const int* cols, const void* vals, long long nnz, void* x_out);
 
 /* Fused-lasso prox without any allocation. The paper has no counterpart to
- * this entry point; it exists for callers that cannot call cudaMalloc, such
- * as code running while a CUDA graph is captured, hosts that hand out device
- * memory only from their own fixed arena, and services that stop allocating
- * after start-up so that no request fails for lack of memory.
+ * this entry point; it exists for callers that cannot call cudaMalloc: hosts
+ * that hand out device memory only from their own fixed arena (memory the
+ * library took behind their back would be missing from it), and services
+ * that stop allocating after start-up so that no request can fail, or wait
+ * on a device-wide synchronisation, for lack of memory.
  *
  * It computes what rihv_prox_fused_lasso computes, up to FP32 rounding order
  * (tv_dims TV prox by inner_iters dual gradient-projection steps from p = 0,
@@ -253,18 +254,22 @@ rihv_status rihv_coo_expand(rihv_handle h, const long long* plane_offsets, const
  * device array inside the library of 6 x 8 MiB + 256 B, reserved on every GPU
  * that loads the library until the process exits. Limits: nx even and >= 2,
  * ny, nz >= 1, nx*ny*nz <= 1,048,576 voxels; larger volumes return
- * RIHV_ERR_UNSUPPORTED_SIZE before any work is queued.
+ * RIHV_ERR_UNSUPPORTED_SIZE before any work is queued (rihv_last_error(NULL)
+ * says why).
  *
- * v, x_out: distinct device complex64 [nz][ny][nx], 16-byte aligned (else
- * RIHV_ERR_INVALID_ARG). stream: a cudaStream_t or NULL. The work is queued on
+ * v, x_out: distinct device complex64 [nz][ny][nx], 16-byte aligned, on the
+ * current device (else RIHV_ERR_INVALID_ARG). stream: a cudaStream_t of the
+ * current device, or NULL. The work is queued on
  * the stream and the call returns; it calls no cudaMalloc, cudaFree or other
  * allocating routine. The first call on each device looks up the scratch's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture. All calls share the one scratch array,
  * which keeps the last call's contents: calls that may overlap on the GPU
  * (different streams, or different host threads) race and must be serialised
- * by the caller. A bounded-wait failure inside the TV kernels only sets a flag
- * in that scratch and is not reported by this call. */
+ * by the caller. A bounded wait inside the TV kernels that gave up (see
+ * rihv_selftest_bounded_wait) cannot be reported by the return code, because
+ * the call returns before the kernels run: it fills x_out with NaN instead,
+ * so a caller that needs to know checks x_out for NaN. */
 rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out, int nx, int ny, int nz,
                                           int tv_dims, float t_l1, float t_tv, int inner_iters,
                                           void* stream);

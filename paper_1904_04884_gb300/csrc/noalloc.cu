@@ -1,14 +1,15 @@
 // rihv_prox_fused_lasso_noalloc: the fused-lasso prox for callers that must
 // not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not allowed inside a capture), hosts whose
-// memory is a fixed arena handed out by another framework, and services that
-// lock their allocator after start-up so that no request can fail on memory.
-// For them this file keeps the prox's scratch (the two ping-pong sets of the
-// TV dual variable) in one statically sized device array that the CUDA driver
-// reserves when the library's module is loaded on a device, and that every
-// call reuses. The caller still passes the input and output volumes.
+// Some callers cannot call cudaMalloc: hosts whose device memory is a fixed
+// arena handed out by another framework (the library may not take memory
+// behind its back), and services that lock their allocator after start-up so
+// that no request can fail, or stall on a device-wide synchronisation, for
+// lack of memory. For them this file keeps the prox's scratch (the two
+// ping-pong sets of the TV dual variable and an error flag) in one statically
+// sized device array that the CUDA driver reserves when the library's module
+// is loaded on a device, and that every call reuses. The caller still passes
+// the input and output volumes.
 //
 // Limit: nx * ny * nz <= kNoAllocMaxVoxels (1,048,576 voxels, e.g.
 // 128 x 128 x 64); the scratch is 6 x 8 MiB + 256 B and stays reserved on
@@ -33,8 +34,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+// The status code carries the outcome; the reason goes to rihv_last_error(NULL).
 rihv_status fail(rihv_status st, const char* why) {
-  (void)why;   // the status code carries the outcome; see include/rihv.h
+  rihv::set_global_error(why);
   return st;
 }
 
@@ -56,13 +58,16 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool is_device(const void* p) {
-  cudaPointerAttributes at{};
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+// A TV kernel whose bounded wait gave up left its flag in the scratch. The
+// call has already returned, so the output itself carries the failure: every
+// voxel becomes NaN, which no finite prox result contains. With the flag
+// clear (the normal case) each thread reads one word and exits.
+__global__ void k_poison_on_timeout(const int* err, float2* x, size_t nvox) {
+  if (*err == 0) return;
+  const float nan = __int_as_float(0x7fc00000);
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    x[i] = make_float2(nan, nan);
 }
 
 }  // namespace
@@ -83,8 +88,20 @@ extern "C" rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out,
   if (!v || !x_out || v == x_out) return fail(RIHV_ERR_INVALID_ARG, "v, x_out: distinct, non-NULL");
   if ((reinterpret_cast<uintptr_t>(v) & 15u) || (reinterpret_cast<uintptr_t>(x_out) & 15u))
     return fail(RIHV_ERR_INVALID_ARG, "v and x_out must be 16-byte aligned");
-  if (!is_device(v) || !is_device(x_out))
-    return fail(RIHV_ERR_INVALID_ARG, "v and x_out must be device memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(RIHV_ERR_CUDA, "cudaGetDevice failed");
+  // The scratch looked up below is the current device's, so the volumes and
+  // the stream must be on that device too (memory of another GPU would be
+  // read through peer access, or fault).
+  for (const void* p : {v, static_cast<const void*>(x_out)}) {
+    const int where = pointer_device(p);
+    if (where == kNotDevicePtr) return fail(RIHV_ERR_INVALID_ARG, "v and x_out must be device memory");
+    if (where != kManagedPtr && where != dev)
+      return fail(RIHV_ERR_INVALID_ARG, "v or x_out lives on another device than the current one");
+  }
+  const int sd = stream_device(stream);
+  if (sd != kLegacyStream && sd != dev)
+    return fail(RIHV_ERR_INVALID_ARG, "the stream belongs to another device than the current one");
 
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess)
@@ -152,5 +169,9 @@ extern "C" rihv_status rihv_prox_fused_lasso_noalloc(const void* v, void* x_out,
   f.kappa = t_l1;
   if (launch_finalize(FIN_PROX, f, s) != cudaSuccess)
     return fail(RIHV_ERR_CUDA, "finalize launch failed");
+  if (tv) {
+    k_poison_on_timeout<<<2 * 152, 256, 0, s>>>(err, static_cast<float2*>(x_out), nvox);
+    if (cudaGetLastError() != cudaSuccess) return fail(RIHV_ERR_CUDA, "launch failed");
+  }
   return RIHV_OK;
 }

@@ -21,6 +21,38 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+namespace rihv {
+
+void set_global_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+int pointer_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kNotDevicePtr;
+  }
+  if (at.type == cudaMemoryTypeManaged) return kManagedPtr;
+  if (at.type != cudaMemoryTypeDevice) return kNotDevicePtr;
+  return at.device;
+}
+
+int stream_device(const void* stream) {
+  if (!stream) return kLegacyStream;
+  int dev = -1;
+  if (cudaStreamGetDevice(static_cast<cudaStream_t>(const_cast<void*>(stream)), &dev) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return kNotDevicePtr;
+  }
+  return dev;
+}
+
+}  // namespace rihv
+
+namespace {
+
 constexpr int kNumStages = 10;
 enum Stage {
   ST_FORWARD = 0, ST_ADJOINT = 1, ST_TV = 2, ST_FINAL = 3, ST_OBJECTIVE = 4, ST_DETECT = 5,
@@ -199,7 +231,13 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 rihv_status check_dev(rihv_ctx* h, const void* p, const char* name) {
   if (!p) return fail(h, RIHV_ERR_INVALID_ARG, "%s is NULL", name);
   if (!aligned16(p)) return fail(h, RIHV_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
-  if (!is_device_ptr(p)) return fail(h, RIHV_ERR_INVALID_ARG, "%s is not device memory", name);
+  const int where = pointer_device(p);
+  if (where == kNotDevicePtr) return fail(h, RIHV_ERR_INVALID_ARG, "%s is not device memory", name);
+  // device memory of another GPU would be read through peer access or fault:
+  // the handle's kernels run on the device it was created on
+  if (where != kManagedPtr && where != h->device)
+    return fail(h, RIHV_ERR_INVALID_ARG, "%s lives on device %d, the handle on device %d", name,
+                where, h->device);
   return RIHV_OK;
 }
 
@@ -763,6 +801,10 @@ rihv_status rihv_destroy(rihv_handle h) {
 
 rihv_status rihv_set_stream(rihv_handle h, void* stream) {
   if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  const int sd = stream_device(stream);
+  if (sd != kLegacyStream && sd != h->device)
+    return fail(h, RIHV_ERR_INVALID_ARG, "the stream belongs to device %d, the handle to device %d",
+                sd, h->device);
   h->stream = static_cast<cudaStream_t>(stream);
   return RIHV_OK;
 }
@@ -831,6 +873,12 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
   CKS(check_solve_args(h, lambda_l1, lambda_tv, iters));
   if (is_device_ptr(x_out) && !aligned16(x_out))
     return fail(h, RIHV_ERR_INVALID_ARG, "x_out is not 16-byte aligned");
+  for (const void* p : {static_cast<const void*>(hologram), x0, static_cast<const void*>(x_out)}) {
+    const int where = p ? pointer_device(p) : kNotDevicePtr;
+    if (where >= 0 && where != h->device)
+      return fail(h, RIHV_ERR_INVALID_ARG, "a buffer lives on device %d, the handle on device %d",
+                  where, h->device);
+  }
   const size_t vb = h->nvox * sizeof(float2);
   const int M = h->opt.check_every;
   CKS(ensure_trace(h, (M > 0) ? iters / M : 0));

@@ -13,6 +13,19 @@
 namespace rihv {
 
 // ---------------------------------------------------------------------------
+// Argument checks shared by the entry points (rihv_api.cu)
+// ---------------------------------------------------------------------------
+constexpr int kNotDevicePtr = -1;   // host, unregistered or invalid pointer
+constexpr int kManagedPtr = -2;     // managed memory (reachable from every device)
+constexpr int kLegacyStream = -3;   // the NULL stream (the current device's)
+// Device that holds p (kNotDevicePtr / kManagedPtr otherwise).
+int pointer_device(const void* p);
+// Device a stream belongs to (kLegacyStream for NULL, kNotDevicePtr on error).
+int stream_device(const void* stream);
+// Message returned by rihv_last_error(NULL).
+void set_global_error(const char* msg);
+
+// ---------------------------------------------------------------------------
 // Sizes and launch shapes
 // ---------------------------------------------------------------------------
 constexpr int kMaxN = 1024;        // largest supported nx, ny

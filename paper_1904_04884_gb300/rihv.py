@@ -356,10 +356,12 @@ class Batch:
 def rihv_prox_fused_lasso_noalloc(v, x_out, nz, ny, nx, tv_dims, t_l1, t_tv, inner_iters,
                                   stream=None):
     """The fused-lasso prox without any device allocation (static scratch in the
-    library; see include/rihv.h). For callers that cannot allocate, e.g. inside
-    a CUDA graph capture or under a fixed memory arena. Volumes up to 1,048,576
-    voxels; nx must be even. Calls that overlap on the GPU share the scratch and
-    race."""
+    library; see include/rihv.h). For callers that cannot allocate: hosts
+    whose device memory is a fixed arena of their own, and services that stop
+    allocating after start-up. Volumes up to 1,048,576 voxels; nx must be
+    even; v, x_out and the stream on the current device. Calls that overlap
+    on the GPU share the scratch and race. A TV wait that gave up leaves x_out
+    all NaN."""
     L = load_library()
     fn = L.rihv_prox_fused_lasso_noalloc
     fn.restype = ctypes.c_int
@@ -371,4 +373,5 @@ def rihv_prox_fused_lasso_noalloc(v, x_out, nz, ny, nx, tv_dims, t_l1, t_tv, inn
             int(nx), int(ny), int(nz), int(tv_dims), float(t_l1), float(t_tv), int(inner_iters),
             getattr(stream, "cuda_stream", stream))
     if st != 0:
-        raise RihvError(st, "rihv_prox_fused_lasso_noalloc failed")
+        msg = L.rihv_last_error(None)
+        raise RihvError(st, msg.decode() if msg else "rihv_prox_fused_lasso_noalloc failed")
