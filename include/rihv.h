@@ -58,7 +58,7 @@ typedef enum {
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
- * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0. */
+ * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0, tv_zchunk 0. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -91,6 +91,13 @@ typedef struct {
                         (fuse_finalize 1, two steps per launch, n_inner >= 2,
                         lambda_tv > 0) and nx, ny <= 1024; otherwise every
                         plane is propagated.                                 */
+  int tv_zchunk;     /* planes per z-chunk of every TV launch (a CTA marches
+                        its tile through one chunk): 0 (default) picks the
+                        chunk per launch kind from the grid and the SM count
+                        (or the autotuner's choice); otherwise
+                        min(nz, 8) <= tv_zchunk <= 256, capped at nz. Results
+                        do not depend on it, except the FISTA restart
+                        product's summation order in the fused finalize.    */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */

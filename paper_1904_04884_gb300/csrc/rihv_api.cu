@@ -448,8 +448,10 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
     const bool last = done + n == k;
     const int b = n == 2 ? ((fused && last) ? 2 : 1) : 0;
     // the fused-finalize launch has its own tile, so its own default chunk
-    a.zchunk = (fused && last) ? zc_final
-                               : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32));
+    a.zchunk = h->opt.tv_zchunk > 0
+                   ? std::min(h->opt.tv_zchunk, h->nz)
+                   : ((fused && last) ? zc_final
+                                      : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32)));
     if (fused && last && (tv_final_ctas(h->nx, h->ny, h->nz, a.zchunk) > h->fin_ctas ||
                           a.zchunk > kTvMaxChunk))
       return fail(h, RIHV_ERR_INVALID_ARG, "z-chunk outside the fused finalize's range");
@@ -649,6 +651,7 @@ void rihv_default_options(rihv_options* o) {
   o->tv_steps_per_launch = 2;
   o->fuse_finalize = 1;
   o->skip_empty_planes = 0;
+  o->tv_zchunk = 0;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -816,7 +819,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       (o->accelerate != 0 && o->accelerate != 1) ||
       (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2) ||
       (o->fuse_finalize != 0 && o->fuse_finalize != 1) ||
-      (o->skip_empty_planes != 0 && o->skip_empty_planes != 1))
+      (o->skip_empty_planes != 0 && o->skip_empty_planes != 1) ||
+      (o->tv_zchunk != 0 && (o->tv_zchunk < std::min(8, h->nz) || o->tv_zchunk > kTvMaxChunk)))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   h->opt = *o;
   return RIHV_OK;
@@ -1136,7 +1140,8 @@ static bool same_options(const rihv_options& a, const rihv_options& o) {
   return a.tv_dims == o.tv_dims && a.restart == o.restart && a.accelerate == o.accelerate &&
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
          a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
-         a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes;
+         a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes &&
+         a.tv_zchunk == o.tv_zchunk;
 }
 
 // Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a

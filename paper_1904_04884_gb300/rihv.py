@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("accelerate", ctypes.c_int), ("n_inner", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
                 ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int),
-                ("fuse_finalize", ctypes.c_int), ("skip_empty_planes", ctypes.c_int)]
+                ("fuse_finalize", ctypes.c_int), ("skip_empty_planes", ctypes.c_int),
+                ("tv_zchunk", ctypes.c_int)]
 
 
 class Particle(ctypes.Structure):

@@ -13,6 +13,7 @@ import torch
 from oracle import rihv_oracle as O
 from paper_1904_04884_gb300 import synth, workloads
 from paper_1904_04884_gb300.rihv import Rihv, RihvError
+from tests import _detect_match as M
 
 pytestmark = pytest.mark.gpu
 
@@ -194,26 +195,23 @@ def test_solve_parity_tiny(tiny_solutions):
 
 
 def test_detection_parity_on_solutions(tiny_solutions):
-    """Detections of the GPU solve match those of the oracle solve: same
-    components (by smallest index and size) and centroids within 0.5 voxel,
-    except components touching a voxel within 1e-3 max|x| of the threshold."""
+    """Detections of the GPU solve match those of the oracle solve one to one
+    by centroid within 0.5 voxel, with equal sizes. A component may differ
+    only if it touches a voxel whose |x| is within 1e-3 max|x| of the
+    threshold in either solution; the number of such exemptions is printed
+    and is 0 on this workload."""
     w, op, b, x, trace, x_ref, tr_ref = tiny_solutions
+    rel = 2.0 / 256.0
     h = handle(op)
-    d_gpu = h.detect(to_dev(x), 2.0 / 256.0, 5)
-    d_ref = O.detect(x_ref, 2.0 / 256.0, 5)
-    m = np.abs(x_ref)
-    edge = np.abs(m - (2.0 / 256.0) * m.max()) < 1e-3 * m.max()
-    exempt = 0
-    ref_by_first = {d["first"]: d for d in d_ref}
-    for d in d_gpu:
-        r = ref_by_first.pop(d["first"], None)
-        if r is None or r["nvox"] != d["nvox"]:
-            exempt += 1
-            continue
-        assert np.max(np.abs(np.subtract(d["centroid"], r["centroid"]))) < 0.5
-    exempt += len(ref_by_first)
-    assert exempt <= max(1, len(d_ref) // 20), (exempt, len(d_ref), int(edge.sum()))
+    d_gpu = h.detect(to_dev(x), rel, 5)
+    d_ref = O.detect(x_ref, rel, 5)
     assert len(d_ref) > 0
+    band = 1e-3 * np.abs(x_ref).max()
+    r = M.compare(x, d_gpu, x_ref, d_ref, rel, band)
+    print(f"detections gpu {r['n_a']} oracle {r['n_b']} matched {r['matched']} "
+          f"exempt {r['exempt']}")
+    assert r["bad"] == [], r
+    assert r["exempt"] == 0, r
 
 
 def test_detection_parity_same_input():
