@@ -1,19 +1,26 @@
 """Benchmark of the fused-lasso FISTA reconstruction on one GB300 per rank.
 
-One step = one complete reconstruction of the 512 x 512 x 128 particle-field
-hologram (200 FISTA iterations, 20 TV dual steps per prox, objective every 10
-iterations, then particle detection), all through the C ABI.
+One step = one complete reconstruction of the 1024 x 1024 x 256 particle-field
+hologram (10,000 discs of 8 um and 200 fibres; 300 FISTA iterations, 20 TV
+dual steps per prox, objective every 10 iterations, then particle
+detection), all through the C ABI.
 
 value  : voxel-iterations/s with hologram and volumes resident in HBM.
 e2e    : the same metric with pinned HOST buffers: the hologram is copied in
          and the volume copied out inside rihv_solve, every step.
 roofline: the TV dual-step kernel (the dominant kernel), from CUDA events the
-         library records around its stages on its own stream during the timed
-         steps; algorithmic bytes 32 (first step) + 56 per later step per voxel.
-cpu_baseline: the FP64 oracle on a bounded sample (two FISTA iterations on a
-         16-plane slab of the same workload), host cores.
-time_to_tolerance: per-hologram time to F*(1+1e-3) on held-out 256x256x64
-         samples, plain FISTA vs the learned warm start + batched CUDA graph.
+         library records around every TV launch on its own stream during the
+         last timed step; algorithmic bytes 56 per voxel for a launch reading p.
+mid    : the same measurement on the 512 x 512 x 128 workload (200 iterations).
+cpu_baseline: the FP64 oracle, as it stands, on the host cores: one process
+         per core (spawned), each solving its own 2-plane slab of the workload,
+         and the same on one core.
+time_to_tolerance: per-hologram time to F*(1+1e-3) on 20 held-out 256x256x64
+         samples: plain FISTA, the learned warm start, batching, and both,
+         every arm with its stop tests inside a CUDA graph.
+batched: the time-resolved 64-frame sequence of mixed sizes (256^2 x 64,
+         512^2 x 128, 768^2 x 192) as batched CUDA graphs against one frame
+         at a time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank reconstructs its own hologram (independent work, no
@@ -43,12 +50,15 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="fista_large_1024x1024x256",
+                   help="named workload of the timed step (default: the 1024x1024x256 case)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-warmstart", action="store_true",
-                   help="skip the time-to-tolerance comparison (plain vs warm start + batched)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the secondary measurements (mid workload, time to tolerance, "
+                        "mixed-size sequence)")
     return p.parse_args()
 
 
@@ -169,39 +179,6 @@ def measured_traffic(nvox, kernel):
     return prof["launch_kinds"]["tv_mid"]["dram_bytes_per_voxel"] * nvox
 
 
-def batched_throughput(n=16, iters=100):
-    """Voxel-iterations/s of n held-out 256x256x64 holograms solved as one
-    batched CUDA graph (one handle each) against the same solves one after
-    another through rihv_solve, plain FISTA from zero, fixed iteration count."""
-    import torch
-    from paper_1904_04884_gb300 import warmstart as W
-    from paper_1904_04884_gb300.rihv import Batch
-
-    dev = torch.device("cuda:0")
-    spec = W.SPEC
-    hs = [W.handle(spec) for _ in range(n)]
-    holo = [W.make_sample(hs[0], spec, 21000 + i, dev)[0] for i in range(n)]
-    outs = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in range(n)]
-    batch = Batch(hs)
-    batch.solve(holo, spec.lam_l1, spec.lam_tv, iters, outs)     # capture the graph
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    batch.solve(holo, spec.lam_l1, spec.lam_tv, iters, outs)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    batch.close()
-    for h, b, x in zip(hs, holo, outs):                            # warm the plain path
-        h.solve(b, spec.lam_l1, spec.lam_tv, 2, x)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for h, b, x in zip(hs, holo, outs):
-        h.solve(b, spec.lam_l1, spec.lam_tv, iters, x)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    vox_it = n * iters * spec.nx * spec.ny * spec.nz
-    return {"holograms": n, "shape": list(spec.shape), "iters": iters,
-            "batched_voxel_iter_s": vox_it / t_batch, "sequential_voxel_iter_s": vox_it / t_seq,
-            "speedup": t_seq / t_batch}
 
 
 def hbm_peak():
@@ -224,27 +201,157 @@ def make_hologram(w, h, torch, dev):
     return b
 
 
-def cpu_baseline_sample(w, iters=2, planes=16):
-    """The FP64 oracle, as it stands, on a slab of the workload: `planes`
-    planes of the same optics, `iters` FISTA iterations. Returns voxel-iter/s."""
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_slab(job):
+    """One worker process: the oracle, as it stands, on its own slab of a
+    workload (the slab's opacity, its hologram by the oracle's forward model,
+    then `iters` FISTA iterations with the workload's weights and dual steps).
+    Returns the wall-clock start and end of the FISTA iterations."""
     from oracle import rihv_oracle as O
-    from paper_1904_04884_gb300 import synth
-    op = O.Optics(w.nx, w.ny, planes, w.wavelength, w.pitch, w.z0, w.dz)
-    a = w.opacity()[:planes].astype(np.float64)
-    b = synth.intensity_hologram(O.forward(a, op), w.sigma, w.noise())
-    t0 = time.perf_counter()
-    O.fista(b.astype(np.float64), op, w.lam_l1, w.lam_tv, iters, w.n_inner)
-    dt = time.perf_counter() - t0
-    return w.nx * w.ny * planes * iters / dt, dt
+    from paper_1904_04884_gb300 import synth, workloads
+    wname, slab, iters = job
+    w = workloads.ALL[wname]
+    op = O.Optics(w.nx, w.ny, slab.shape[0], w.wavelength, w.pitch, w.z0, w.dz)
+    b = synth.intensity_hologram(O.forward(slab.astype(np.float64), op), w.sigma, w.noise())
+    t0 = time.time()
+    O.fista(b.astype(np.float64), op, w.lam_l1, w.lam_tv, iters, w.n_inner, dims=w.tv_dims)
+    return t0, time.time()
 
 
-def time_to_tolerance(seeds=(20001, 20002, 20003, 20004), tol=1e-3):
-    """Per-hologram wall time to reach F* (1 + tol) on held-out 256x256x64
-    samples: plain FISTA from zero (stop test every 10 iterations) against the
-    learned warm start plus all holograms solved together as one batched CUDA
-    graph in which every hologram keeps its own stop test (it stops at its own
-    first check that meets the tolerance). F* is the objective of a
-    600-iteration plain solve."""
+def host_cores():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+class OraclePool:
+    """`cores` spawned worker processes, one oracle slab each per round."""
+
+    def __init__(self, w, cores, planes=1):
+        import multiprocessing as mp
+        self.w = w
+        self.cores = cores
+        vol = w.opacity()
+        span = max(1, w.nz - planes + 1)
+        self.slabs = [np.ascontiguousarray(vol[(i * planes) % span:(i * planes) % span + planes])
+                      for i in range(cores)]
+        self.vox = w.nx * w.ny * planes
+        self.pool = mp.get_context("spawn").Pool(cores) if cores > 1 else None
+
+    def run(self, iters, n=None):
+        """One round on n slabs (all cores by default); returns the wall time
+        from the first worker's start to the last one's end."""
+        jobs = [(self.w.name, s, iters) for s in self.slabs[:n or self.cores]]
+        res = self.pool.map(_oracle_slab, jobs, chunksize=1) if self.pool and len(jobs) > 1 \
+            else [_oracle_slab(j) for j in jobs]
+        return max(e for _, e in res) - min(s for s, _ in res)
+
+    def close(self):
+        if self.pool:
+            self.pool.close()
+            self.pool.join()
+
+
+def cpu_baseline(w, iters=2):
+    """The oracle on every host core (one spawned process per core, each
+    solving its own one-plane slab of the workload for `iters` iterations)
+    and on one core (one slab alone)."""
+    cores = host_cores()
+    pool = OraclePool(w, cores)
+    try:
+        pool.run(1, n=min(cores, 2))                  # workers up, modules imported
+        t_all = pool.run(iters)
+        t_one = pool.run(iters, n=1)
+    finally:
+        pool.close()
+    value = cores * pool.vox * iters / t_all
+    one = pool.vox * iters / t_one
+    sample = (f"{iters} FISTA iterations (K={w.n_inner}) per process on its own "
+              f"{w.nx}x{w.ny}x1 slab of the same workload, {cores} processes in parallel "
+              f"({t_all:.1f} s wall); numpy FP64, one thread per process")
+    return {"value": value, "unit": "voxel-iter/s", "cores": cores, "kind": "oracle",
+            "sample": sample, "one_core": {"value": one, "cores": 1, "seconds": t_one}}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, each step one
+    FISTA iteration per core on its own one-plane slab of the same workload."""
+    if rank != 0:
+        return
+    from paper_1904_04884_gb300 import workloads
+    w = workloads.ALL[args.workload]
+    cores = host_cores()
+    pool = OraclePool(w, cores)
+    try:
+        for _ in range(args.warmup):
+            pool.run(1)
+        dt = sum(pool.run(1) for _ in range(args.steps))
+    finally:
+        pool.close()
+    value = cores * pool.vox * args.steps / dt
+    sample = (f"1 FISTA iteration (K={w.n_inner}) per process on its own {w.nx}x{w.ny}x1 slab "
+              f"per step, {cores} processes")
+    line = {
+        "impl": "reference", "metric": "voxel-iterations/s", "value": value,
+        "unit": "voxel-iter/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "iters": w.iters,
+                   "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
+                   "parallelism": f"replicas x{world}", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Secondary measurements (one GPU)
+# ---------------------------------------------------------------------------
+
+def solve_rate(w, dev, steps=3, warmup=1):
+    """Voxel-iterations/s of full solves (+ detection) of workload w, device
+    buffers, CUDA events on the library's stream."""
+    import torch
+    from paper_1904_04884_gb300.rihv import Rihv
+    stream = torch.cuda.Stream(device=dev)
+    h = Rihv(*w.optics_tuple(), stream=stream)
+    h.set_options(tv_dims=w.tv_dims, n_inner=w.n_inner, check_every=10)
+    b = torch.from_numpy(make_hologram(w, h, torch, dev)).to(dev)
+    x = torch.empty(w.shape, dtype=torch.complex64, device=dev)
+    trace = torch.empty(max(1, w.iters // 10), dtype=torch.float64, device=dev)
+    ndet = 0
+    for _ in range(warmup):
+        h.solve(b, w.lam_l1, w.lam_tv, w.iters, x, trace=trace)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        h.solve(b, w.lam_l1, w.lam_tv, w.iters, x, trace=trace)
+        ndet = len(h.detect(x, 2.0 / 256.0, 5))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h.close()
+    return {"workload": w.name, "value": w.nvox * w.iters * steps / (ms / 1e3),
+            "unit": "voxel-iter/s", "ms_per_step": ms / steps, "steps": steps,
+            "detections": ndet}
+
+
+def time_to_tolerance(n_seeds=20, tol=1e-3, max_iters=400):
+    """Per-hologram wall time to F* (1 + tol), checked every 10 iterations, on
+    held-out 256x256x64 samples (seeds 20001...), F* the objective of a
+    600-iteration plain solve. Four arms, every one with its stop tests inside
+    a CUDA graph (conditional nodes, no host round trip): plain FISTA from
+    zero one hologram at a time; the learned warm start one at a time
+    (network inference included); plain FISTA with all holograms in one
+    batched graph; warm start and batched graph together."""
     import torch
     from paper_1904_04884_gb300 import warmstart as W
     from paper_1904_04884_gb300.rihv import Batch
@@ -254,81 +361,74 @@ def time_to_tolerance(seeds=(20001, 20002, 20003, 20004), tol=1e-3):
     spec = W.SPEC
     net = WarmStartUNet.load(W.DEFAULT_WEIGHTS)
     h = W.handle(spec)
+    seeds = list(range(20001, 20001 + n_seeds))
     samples = [W.make_sample(h, spec, s, dev) for s in seeds]
     f_star = [W.reference_objective(h, b, spec) for b, _ in samples]
-    plain_t, plain_it, warm_it = [], [], []
-    for (b, hb), fs in zip(samples, f_star):
-        it, t, _ = W.iterations_to_tolerance(h, b, spec, None, fs, tol)
-        plain_it.append(it)
-        plain_t.append(t)
-        x0 = torch.empty(spec.shape, dtype=torch.complex64, device=dev)
-        net.predict(hb, x0)
-        it, _, _ = W.iterations_to_tolerance(h, b, spec, x0, fs, tol)
-        warm_it.append(it)
-    # every hologram keeps its own stop test inside the batched graph
+    h.close()
+    holos = [b for b, _ in samples]
     hs = [W.handle(spec, check_every=10, f_star=fs, tol=tol) for fs in f_star]
-    batch = Batch(hs)
-    iters = 600
     x0s = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in seeds]
     outs = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in seeds]
 
-    def warm_batched():
-        for (b, hb), x0 in zip(samples, x0s):
+    def predict_all():
+        for (_, hb), x0 in zip(samples, x0s):
             net.predict(hb, x0)
-        batch.solve([b for b, _ in samples], spec.lam_l1, spec.lam_tv, iters, outs, x0s=x0s)
+
+    def timed(fn):
+        fn()                                   # captures the graphs
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
 
-    warm_batched()                       # capture the graph
-    t0 = time.perf_counter()
-    reps = 3
-    for _ in range(reps):
-        warm_batched()
-    t_wb = (time.perf_counter() - t0) / reps / len(seeds)
-    batch_its = batch.iterations()
+    t_inf = timed(predict_all) / n_seeds
+    singles = [Batch([hh]) for hh in hs]
+
+    def plain_single():
+        for bt, b, x in zip(singles, holos, outs):
+            bt.solve([b], spec.lam_l1, spec.lam_tv, max_iters, [x])
+
+    def warm_single():
+        for bt, b, x0, x in zip(singles, holos, x0s, outs):
+            bt.solve([b], spec.lam_l1, spec.lam_tv, max_iters, [x], x0s=[x0])
+
+    t_ps = timed(plain_single)
+    it_plain = [bt.iterations()[0] for bt in singles]
+    t_ws = timed(warm_single)
+    it_warm = [bt.iterations()[0] for bt in singles]
+    for bt in singles:
+        bt.close()
+    batch = Batch(hs)
+    t_pb = timed(lambda: batch.solve(holos, spec.lam_l1, spec.lam_tv, max_iters, outs))
+    it_pb = batch.iterations()
+    t_wb = timed(lambda: batch.solve(holos, spec.lam_l1, spec.lam_tv, max_iters, outs, x0s=x0s))
+    it_wb = batch.iterations()
     batch.close()
-    t_plain = float(np.mean(plain_t))
+    for hh in hs:
+        hh.close()
+    assert net.errors() == 0
+    plain, warm = t_ps / n_seeds, t_ws / n_seeds + t_inf
+    pb, wb = t_pb / n_seeds, t_wb / n_seeds + t_inf
     return {"workload": "warmstart_256x256x64 (lambda 0.01 / 0.005, K = 20)",
-            "tolerance": tol, "seeds": list(seeds), "plain_iters": plain_it,
-            "warm_iters": warm_it, "batched_iters": batch_its,
-            "plain_s_per_hologram": t_plain, "warm_batched_s_per_hologram": t_wb,
-            "speedup": t_plain / t_wb}
+            "tolerance": tol, "seeds": [seeds[0], seeds[-1]], "n_holograms": n_seeds,
+            "plain_iters": it_plain, "warm_iters": it_warm,
+            "plain_batched_iters": it_pb, "warm_batched_iters": it_wb,
+            "mean_plain_iters": float(np.mean(it_plain)), "mean_warm_iters": float(np.mean(it_warm)),
+            "inference_s_per_hologram": t_inf,
+            "plain_s_per_hologram": plain, "warm_s_per_hologram": warm,
+            "plain_batched_s_per_hologram": pb, "warm_batched_s_per_hologram": wb,
+            "speedup_warm_only": plain / warm, "speedup_batch_only": plain / pb,
+            "speedup": plain / wb}
 
 
-def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle on the host cores, each step a bounded
-    sample (one FISTA iteration on a 16-plane slab) of the same workload."""
-    if rank != 0:
-        return
-    from paper_1904_04884_gb300 import workloads
-    from oracle import rihv_oracle as O
-    from paper_1904_04884_gb300 import synth
-    w = workloads.MID
-    planes = 16
-    op = O.Optics(w.nx, w.ny, planes, w.wavelength, w.pitch, w.z0, w.dz)
-    a = w.opacity()[:planes].astype(np.float64)
-    b = synth.intensity_hologram(O.forward(a, op), w.sigma, w.noise()).astype(np.float64)
-    for _ in range(args.warmup):
-        O.fista(b, op, w.lam_l1, w.lam_tv, 1, w.n_inner)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.fista(b, op, w.lam_l1, w.lam_tv, 1, w.n_inner)
-    dt = time.perf_counter() - t0
-    value = w.nx * w.ny * planes * args.steps / dt
-    sample = f"1 FISTA iteration (K={w.n_inner}) on a {w.nx}x{w.ny}x{planes} slab per step"
-    line = {
-        "impl": "reference", "metric": "voxel-iterations/s", "value": value,
-        "unit": "voxel-iter/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "iters": w.iters,
-                   "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
-                   "parallelism": f"replicas x{world}", "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+def mixed_sequence(frames=64, iters=50, slots=4):
+    """The time-resolved mixed-size sequence: batched graphs against one frame
+    at a time (paper_1904_04884_gb300.sequence)."""
+    from paper_1904_04884_gb300 import sequence
+    r = sequence.run(frames, iters, slots, log=lambda *_: None)
+    r.pop("hologram_seconds", None)
+    return r
 
 
 def main():
@@ -352,7 +452,7 @@ def main():
     assert torch.cuda.is_available(), "bench.py needs a GPU"
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workloads.MID
+    w = workloads.ALL[args.workload]
     stream = torch.cuda.Stream(device=dev)
     h = Rihv(*w.optics_tuple(), stream=stream)
     h.set_options(tv_dims=w.tv_dims, n_inner=w.n_inner, check_every=10)
@@ -462,20 +562,23 @@ def main():
     coo = {"nnz": nnz, "sparsity": 1.0 - nnz / w.nvox, "bytes": 16 * nnz + 8 * (w.nz + 1),
            "dense_bytes": 8 * w.nvox, "compact_ms": (t1 - t0) * 1e3, "expand_ms": (t2 - t1) * 1e3,
            "round_trip_exact": bool(torch.equal(back, x_dev))}
-    del back, rows, cols, vals
+    del back, rows, cols, vals, b_host, x_host
+    h.close()
+    del x_dev, b_dev
+    torch.cuda.empty_cache()
 
-    ttt = None
-    batched = None
-    if not args.no_warmstart:
+    mid = ttt = batched = None
+    if not args.no_extras and world == 1:
+        if w.name != workloads.MID.name:
+            mid = solve_rate(workloads.MID, dev)
+        torch.cuda.empty_cache()
         ttt = time_to_tolerance()
-        batched = batched_throughput()
+        torch.cuda.empty_cache()
+        batched = mixed_sequence()
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt = cpu_baseline_sample(w)
-        cpu = {"value": v, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
-               "sample": f"2 FISTA iterations (K={w.n_inner}) on a {w.nx}x{w.ny}x16 slab "
-                         f"of the same workload, {dt:.1f} s, numpy FP64 single thread"}
+        cpu = cpu_baseline(w)
 
     line = {
         "metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s",
@@ -485,9 +588,9 @@ def main():
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "iters": w.iters,
                    "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
                    "step": "full FISTA solve + objective every 10 iters + detection",
-                   "l2": "inputs larger than L2 (268 MB per volume)",
+                   "l2": f"inputs larger than L2 ({8 * w.nvox / 1e6:.0f} MB per volume)",
                    "detections": ndet, "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e_value, "unit": "voxel-iter/s",
+        "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(w.nx * w.ny * 4),
                 "d2h_bytes_per_step": int(w.nvox * 8 + (w.iters // 10) * 8)},
         "gpu_launches": int(total_launches),
@@ -500,6 +603,7 @@ def main():
                      "avg_launch_ms": avg_launch_s * 1e3,
                      "tv_launch_kinds": kinds},
         "stages_ms_per_step": {k: stages[k][0] / args.steps for k in main_stages},
+        "mid": mid,
         "time_to_tolerance": ttt,
         "batched": batched,
         "coo": coo,

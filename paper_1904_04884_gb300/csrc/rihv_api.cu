@@ -1208,7 +1208,7 @@ static rihv_status batch_capture_cond(rihv_batch b, float l1, float ltv, int ite
     cudaGraph_t g = nullptr;
     cudaGraphNode_t prev = nullptr, node = nullptr;
     int check = 0;
-    h->batch_chunks = true;
+    h->batch_chunks = n > 1;   // a batch of one runs like a lone solve
     st = capture_graph(h, b->branch[i], &g, [&] { return enqueue_setup(h, warm); });
     if (st != RIHV_OK) {
       h->batch_chunks = false;
@@ -1306,7 +1306,7 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     long long before[kNumStages];
     for (int s = 0; s < kNumStages; ++s) before[s] = h->stage_launches[s];
     cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-    h->batch_chunks = true;
+    h->batch_chunks = n > 1;   // a batch of one runs like a lone solve
     st = enqueue_setup(h, warm);
     int check = 0;
     for (int k = 1; k <= iters && st == RIHV_OK; ++k) st = enqueue_iteration(h, k, l1, ltv, &check);
