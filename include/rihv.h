@@ -176,6 +176,26 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
 rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_vox,
                         rihv_particle* out, int max_out, int* n_out);
 
+/* The same detection on a volume's per-plane COO form (Section 2: volumes
+ * are stored plane by plane as lists of their non-zero elements; see
+ * rihv_coo_compact for the layout), with work in proportion to the nnz
+ * listed entries instead of the nx*ny*nz voxels: the threshold is taken over
+ * the listed values (the maximum of |x| is the same), the entries above it
+ * are compacted into an ascending list of linear voxel indices, and the
+ * components are formed over that list, each entry finding its 26-neighbours
+ * by binary search. Gives the particles rihv_detect gives on the expanded
+ * volume (same components, order and sizes; centroids up to FP64 summation
+ * order). plane_offsets: device int64 [nz+1], checked on the host first (0
+ * first, nnz last, non-decreasing, at most nx*ny per plane; else
+ * RIHV_ERR_INVALID_ARG). rows, cols: device int32 [nnz]; vals: device
+ * complex64 [nnz] (16-byte aligned); nnz < 2^31 (else
+ * RIHV_ERR_UNSUPPORTED_SIZE). nnz = 0 finds nothing. out, max_out, n_out as
+ * for rihv_detect. Synchronises the stream; the first call (and one with
+ * more entries than any before) allocates the list scratch. */
+rihv_status rihv_detect_coo(rihv_handle h, const long long* plane_offsets, const int* rows,
+                            const int* cols, const void* vals, long long nnz, float rel_thresh,
+                            int min_vox, rihv_particle* out, int max_out, int* n_out);
+
 /* Batched solves. A batch groups handles (each with its own grid, optics,
  * options and scratch; a handle may appear once) whose holograms are solved
  * together: rihv_batch_solve runs every handle's complete FISTA solve (the

@@ -142,6 +142,7 @@ struct rihv_ctx {
   int* occ = nullptr;          // [nz] planes of x_k / y_{k+1} with a non-zero voxel
   CUtensorMap tm_pa[3][3], tm_pb[3][3];   // [one-step, two-step, fused-finalize box]
   DetectWork det{};
+  CooDetectWork cdet{};
   std::vector<void*> allocs;
 
   // profiling
@@ -621,6 +622,62 @@ rihv_status enqueue_iteration(rihv_ctx* h, int k, float lambda_l1, float lambda_
   return RIHV_OK;
 }
 
+// Per-component sums and first indices for ncomp components (grown on demand).
+rihv_status ensure_stats(rihv_ctx* h, int ncomp) {
+  DetectWork& w = h->det;
+  if (static_cast<size_t>(ncomp) <= w.capacity) return RIHV_OK;
+  if (w.stats) cudaFree(w.stats);
+  if (w.first) cudaFree(w.first);
+  w.stats = nullptr;
+  w.first = nullptr;
+  w.capacity = 0;
+  const size_t cap = std::max<size_t>(ncomp, 1024);
+  if (cudaMalloc(&w.stats, cap * 5 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&w.first, cap * sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RIHV_ERR_OOM, "detection stats allocation failed");
+  }
+  w.capacity = cap;
+  return RIHV_OK;
+}
+
+// Reads the ncomp components' sums back, drops those of <= min_vox voxels and
+// writes the rest (in component order, i.e. by smallest voxel index).
+rihv_status emit_particles(rihv_ctx* h, int ncomp, int min_vox, rihv_particle* out, int max_out,
+                           int* n_out) {
+  std::vector<double> st(static_cast<size_t>(ncomp) * 5);
+  std::vector<long long> first(ncomp);
+  int err = 0;
+  if (ncomp > 0) {
+    CK(cudaMemcpyAsync(st.data(), h->det.stats, st.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(first.data(), h->det.first, first.size() * sizeof(long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaMemcpyAsync(&err, h->det_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err) return fail(h, RIHV_ERR_TIMEOUT, "union-find exceeded its iteration bound");
+  int n = 0;
+  for (int c = 0; c < ncomp; ++c) {
+    const double* s = &st[static_cast<size_t>(c) * 5];
+    const int cnt = static_cast<int>(s[4] + 0.5);
+    if (cnt <= min_vox) continue;
+    if (n < max_out) {
+      rihv_particle& p = out[n];
+      p.cx = s[1] / s[0];
+      p.cy = s[2] / s[0];
+      p.cz = s[3] / s[0];
+      p.weight = s[0];
+      p.first = first[c];
+      p.nvox = cnt;
+      p.pad_ = 0;
+    }
+    ++n;
+  }
+  *n_out = n;
+  return RIHV_OK;
+}
+
 // After the stream has finished: TV wait failures and non-finite reductions.
 rihv_status read_solve_errors(rihv_ctx* h) {
   DevScalars hs{};
@@ -796,6 +853,11 @@ rihv_status rihv_destroy(rihv_handle h) {
   if (h->det.ncomp) cudaFree(h->det.ncomp);
   if (h->det.stats) cudaFree(h->det.stats);
   if (h->det.first) cudaFree(h->det.first);
+  for (void* p : {static_cast<void*>(h->cdet.lin), static_cast<void*>(h->cdet.wgt),
+                  static_cast<void*>(h->cdet.label), static_cast<void*>(h->cdet.cid),
+                  static_cast<void*>(h->cdet.block_counts), static_cast<void*>(h->cdet.maxbits),
+                  static_cast<void*>(h->cdet.nhits), static_cast<void*>(h->cdet.ncomp)})
+    if (p) cudaFree(p);
   if (h->trace) cudaFree(h->trace);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -999,52 +1061,70 @@ rihv_status rihv_detect(rihv_handle h, const void* x, float rel_thresh, int min_
   int ncomp = 0;
   CK(detect_label(static_cast<const float2*>(x), h->nx, h->ny, h->nz, rel_thresh, w, h->det_err,
                   &ncomp, h->stream));
-  if (static_cast<size_t>(ncomp) > w.capacity) {
-    if (w.stats) cudaFree(w.stats);
-    if (w.first) cudaFree(w.first);
-    w.stats = nullptr;
-    w.first = nullptr;
+  CKS(ensure_stats(h, ncomp));
+  if (ncomp > 0)
+    CK(detect_stats(static_cast<const float2*>(x), h->nx, h->ny, h->nz, w, ncomp, h->stream));
+  return emit_particles(h, ncomp, min_vox, out, max_out, n_out);
+}
+
+rihv_status rihv_detect_coo(rihv_handle h, const long long* plane_offsets, const int* rows,
+                            const int* cols, const void* vals, long long nnz, float rel_thresh,
+                            int min_vox, rihv_particle* out, int max_out, int* n_out) {
+  if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
+  if (!plane_offsets || nnz < 0 || (nnz > 0 && (!rows || !cols || !vals)) || !n_out ||
+      (max_out > 0 && !out) || max_out < 0 || min_vox < 0 || !(rel_thresh >= 0.f) ||
+      !std::isfinite(rel_thresh))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid detect arguments");
+  if (nnz >= static_cast<long long>(INT32_MAX))
+    return fail(h, RIHV_ERR_UNSUPPORTED_SIZE, "more non-zeros than int32 list positions");
+  CKS(check_dev(h, plane_offsets, "plane_offsets"));
+  *n_out = 0;
+  if (nnz == 0) return RIHV_OK;
+  CKS(check_dev(h, rows, "rows"));
+  CKS(check_dev(h, cols, "cols"));
+  CKS(check_dev(h, vals, "vals"));
+  // plane offsets are checked on the host before any entry is read
+  std::vector<long long> off(static_cast<size_t>(h->nz) + 1);
+  CK(cudaMemcpyAsync(off.data(), plane_offsets, off.size() * sizeof(long long),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (off[0] != 0 || off[h->nz] != nnz)
+    return fail(h, RIHV_ERR_INVALID_ARG, "plane offsets must run from 0 to nnz");
+  for (int k = 0; k < h->nz; ++k)
+    if (off[k + 1] < off[k] || off[k + 1] - off[k] > static_cast<long long>(h->nxy))
+      return fail(h, RIHV_ERR_INVALID_ARG, "plane offsets must be non-decreasing, <= nx*ny per plane");
+  CooDetectWork& w = h->cdet;
+  if (static_cast<size_t>(nnz) > w.capacity) {
+    for (void* p : {static_cast<void*>(w.lin), static_cast<void*>(w.wgt),
+                    static_cast<void*>(w.label), static_cast<void*>(w.cid),
+                    static_cast<void*>(w.block_counts)})
+      if (p) cudaFree(p);
+    w.lin = nullptr; w.wgt = nullptr; w.label = nullptr; w.cid = nullptr; w.block_counts = nullptr;
     w.capacity = 0;
-    const size_t cap = std::max<size_t>(ncomp, 1024);
-    if (cudaMalloc(&w.stats, cap * 5 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&w.first, cap * sizeof(long long)) != cudaSuccess) {
+    const size_t cap = std::max<size_t>(static_cast<size_t>(nnz), 1 << 16);
+    if (cudaMalloc(&w.lin, cap * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&w.wgt, cap * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&w.label, cap * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&w.cid, cap * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&w.block_counts, (cap / 1024 + 1) * sizeof(unsigned)) != cudaSuccess ||
+        (!w.maxbits && cudaMalloc(&w.maxbits, sizeof(unsigned)) != cudaSuccess) ||
+        (!w.nhits && cudaMalloc(&w.nhits, sizeof(int)) != cudaSuccess) ||
+        (!w.ncomp && cudaMalloc(&w.ncomp, sizeof(int)) != cudaSuccess)) {
       cudaGetLastError();
-      return fail(h, RIHV_ERR_OOM, "detection stats allocation failed");
+      return fail(h, RIHV_ERR_OOM, "detection list allocation failed");
     }
     w.capacity = cap;
   }
-  std::vector<double> st(static_cast<size_t>(ncomp) * 5);
-  std::vector<long long> first(ncomp);
-  int err = 0;
-  if (ncomp > 0) {
-    CK(detect_stats(static_cast<const float2*>(x), h->nx, h->ny, h->nz, w, ncomp, h->stream));
-    CK(cudaMemcpyAsync(st.data(), w.stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaMemcpyAsync(first.data(), w.first, first.size() * sizeof(long long),
-                       cudaMemcpyDeviceToHost, h->stream));
-  }
-  CK(cudaMemcpyAsync(&err, h->det_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  if (err) return fail(h, RIHV_ERR_TIMEOUT, "union-find exceeded its iteration bound");
-  int n = 0;
-  for (int c = 0; c < ncomp; ++c) {
-    const double* s = &st[static_cast<size_t>(c) * 5];
-    const int cnt = static_cast<int>(s[4] + 0.5);
-    if (cnt <= min_vox) continue;
-    if (n < max_out) {
-      rihv_particle& p = out[n];
-      p.cx = s[1] / s[0];
-      p.cy = s[2] / s[0];
-      p.cz = s[3] / s[0];
-      p.weight = s[0];
-      p.first = first[c];
-      p.nvox = cnt;
-      p.pad_ = 0;
-    }
-    ++n;
-  }
-  *n_out = n;
-  return RIHV_OK;
+  StageScope scope(h, ST_DETECT, 9);
+  int m = 0, ncomp = 0;
+  CK(detect_coo_hits(plane_offsets, rows, cols, static_cast<const float2*>(vals), nnz, h->nx,
+                     h->ny, h->nz, rel_thresh, w, &m, h->stream));
+  if (m > 0)
+    CK(detect_coo_label(m, h->nx, h->ny, w, h->det_err, &ncomp, h->stream));
+  CKS(ensure_stats(h, ncomp));
+  if (ncomp > 0)
+    CK(detect_coo_stats(m, h->nx, h->ny, w, ncomp, h->det.stats, h->det.first, h->stream));
+  return emit_particles(h, ncomp, min_vox, out, max_out, n_out);
 }
 
 rihv_status rihv_selftest_bounded_wait(rihv_handle h, int polls) {

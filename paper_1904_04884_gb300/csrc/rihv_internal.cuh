@@ -232,6 +232,31 @@ cudaError_t detect_label(const float2* x, int nx, int ny, int nz, float rel, Det
 cudaError_t detect_stats(const float2* x, int nx, int ny, int nz, DetectWork& w, int ncomp,
                          cudaStream_t s);
 
+// Detection on a per-plane COO form (work in proportion to the non-zeros).
+struct CooDetectWork {
+  long long* lin = nullptr;      // [capacity] linear indices of the entries above threshold
+  float* wgt = nullptr;          // [capacity] their |x|
+  int* label = nullptr;          // [capacity] union-find parents (list positions)
+  int* cid = nullptr;            // [capacity] compact component id, valid at roots
+  unsigned* block_counts = nullptr;  // [capacity / 1024 + 1]
+  unsigned* maxbits = nullptr;   // [1]
+  int* nhits = nullptr;          // [1]
+  int* ncomp = nullptr;          // [1]
+  size_t capacity = 0;           // entries (nnz) the buffers hold
+};
+// Threshold over the nnz > 0 listed values, compaction of the entries above
+// it; *m_host receives their number (synchronises the stream).
+cudaError_t detect_coo_hits(const long long* plane_off, const int* rows, const int* cols,
+                            const float2* vals, long long nnz, int nx, int ny, int nz, float rel,
+                            CooDetectWork& w, int* m_host, cudaStream_t s);
+// Union-find over the m > 0 compacted entries; *ncomp_host receives the
+// number of components (synchronises the stream).
+cudaError_t detect_coo_label(int m, int nx, int ny, CooDetectWork& w, int* err_dev,
+                             int* ncomp_host, cudaStream_t s);
+// First indices and FP64 sums [ncomp][5] of the components.
+cudaError_t detect_coo_stats(int m, int nx, int ny, CooDetectWork& w, int ncomp, double* stats,
+                             long long* first, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Warm-start network convolutions (conv_kernels.cu)
 // ---------------------------------------------------------------------------

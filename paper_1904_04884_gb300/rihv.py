@@ -23,12 +23,21 @@ STATUS = {0: "RIHV_OK", 1: "RIHV_ERR_INVALID_ARG", 2: "RIHV_ERR_CUDA", 3: "RIHV_
 
 EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stream",
            "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
-           "rihv_solve", "rihv_detect", "rihv_set_profiling", "rihv_stage_times",
+           "rihv_solve", "rihv_detect", "rihv_detect_coo", "rihv_set_profiling", "rihv_stage_times",
            "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
            "rihv_batch_destroy", "rihv_autotune"]
 
 STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup",
           "tv_first", "tv_mid", "tv_final"]
+
+
+def _particles(arr, n, max_out):
+    out = []
+    for k in range(min(n, max_out)):
+        p = arr[k]
+        out.append(dict(centroid=(p.cx, p.cy, p.cz), nvox=p.nvox, weight=p.weight,
+                        first=p.first))
+    return out
 
 
 class RihvError(RuntimeError):
@@ -77,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_prox_fused_lasso": (i, [H, vp, f, f, i, vp]),
         "rihv_solve": (i, [H, vp, f, f, i, vp, vp, vp, ctypes.POINTER(i)]),
         "rihv_detect": (i, [H, vp, f, i, ctypes.POINTER(Particle), i, ctypes.POINTER(i)]),
+        "rihv_detect_coo": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, f, i,
+                                ctypes.POINTER(Particle), i, ctypes.POINTER(i)]),
         "rihv_set_profiling": (i, [H, i]),
         "rihv_stage_times": (i, [H, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "rihv_step_size": (i, [H, ctypes.POINTER(d)]),
@@ -220,12 +231,22 @@ class Rihv:
         self._check(self.L.rihv_detect(
             self.h, _ptr(x, device=True, dtype="complex64", numel=self.nvox, name="x") or None,
             float(rel_thresh), int(min_vox), arr, int(max_out), ctypes.byref(n)), self.h)
-        out = []
-        for k in range(min(n.value, max_out)):
-            p = arr[k]
-            out.append(dict(centroid=(p.cx, p.cy, p.cz), nvox=p.nvox, weight=p.weight,
-                            first=p.first))
-        return out
+        return _particles(arr, n.value, max_out)
+
+    def rihv_detect_coo(self, offsets, rows, cols, vals, rel_thresh=2.0 / 256.0, min_vox=5,
+                        max_out=1 << 20):
+        """Detection on a per-plane COO form (as rihv_coo_compact returns it);
+        the same particles as rihv_detect on the expanded volume."""
+        n = ctypes.c_int()
+        nnz = int(rows.numel())
+        arr = (Particle * max(1, max_out))()
+        self._check(self.L.rihv_detect_coo(
+            self.h, _ptr(offsets, device=True, dtype="int64", numel=self.nz + 1, name="offsets"),
+            _ptr(rows, device=True, dtype="int32", name="rows") if nnz else None,
+            _ptr(cols, device=True, dtype="int32", name="cols") if nnz else None,
+            _ptr(vals, device=True, dtype="complex64", name="vals") if nnz else None, nnz,
+            float(rel_thresh), int(min_vox), arr, int(max_out), ctypes.byref(n)), self.h)
+        return _particles(arr, n.value, max_out)
 
     def rihv_coo_compact(self, x=None):
         """Per-plane COO form of x (None: the last solve's result) as device
@@ -261,6 +282,7 @@ class Rihv:
             _ptr(vals, device=True, dtype="complex64", name="vals") if n else None, n,
             _ptr(x_out, device=True, dtype="complex64", numel=self.nvox, name="x_out")), self.h)
 
+    detect_coo = rihv_detect_coo
     coo_compact = rihv_coo_compact
     coo_expand = rihv_coo_expand
 
