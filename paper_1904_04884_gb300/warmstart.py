@@ -54,13 +54,18 @@ class SampleSpec:
 SPEC = SampleSpec()
 
 
-def opacity(spec: SampleSpec, seed: int):
-    """Seeded opacity volume: 200-2,000 discs of 8-20 um; returns (vol, sigma)."""
+def discs(spec: SampleSpec, seed: int):
+    """The seeded sample's discs (200-2,000 of 8-20 um) and hologram noise sigma."""
     st = synth.Stream(seed)
     n = int(st.integers(1, 1801)[0]) + 200
     sigma = float(st.uniform(1, 0.01, 0.03)[0])
+    return synth.random_discs(st, spec.shape, n, 8.0, 20.0, spec.pitch * 1e6, False), sigma
+
+
+def opacity(spec: SampleSpec, seed: int):
+    """Seeded opacity volume of the sample's discs; returns (vol, sigma)."""
+    parts, sigma = discs(spec, seed)
     vol = np.zeros(spec.shape, np.float32)
-    parts = synth.random_discs(st, spec.shape, n, 8.0, 20.0, spec.pitch * 1e6, False)
     synth.rasterise_discs(vol, parts)
     return vol, sigma
 
