@@ -115,7 +115,15 @@ SLAB = Workload("slab_512x512x256", 512, 512, 256, 532e-9, 5e-6, 5e-3, 50e-6,
                 n_discs=1000, d_um=(10.0, 20.0), at_voxel_centres=False, sigma=0.02,
                 iters=100, lam_l1=0.1, lam_tv=0.1, n_inner=5, tv_dims=2, z_slab=(96, 160))
 
-ALL = {w.name: w for w in (TINY, MID, LARGE, PAPER_TURBULENCE, SLAB)}
+# The paper's 10^9-voxel example (Sections 1 and 2: 1024 x 1024 pixels and
+# 1024 planes, 1,000 particles per hologram): 25 um planes at the large
+# workload's optics, discs of 8-20 um, the paper's turbulence-case weights
+# (its example names none), 100 iterations.
+GIGA = Workload("fista_giga_1024x1024x1024", 1024, 1024, 1024, 532e-9, 5e-6, 5e-3, 25e-6,
+                n_discs=1000, d_um=(8.0, 20.0), at_voxel_centres=False, sigma=0.02,
+                iters=100, lam_l1=0.5, lam_tv=0.2, n_inner=20)
+
+ALL = {w.name: w for w in (TINY, MID, LARGE, PAPER_TURBULENCE, SLAB, GIGA)}
 
 
 def shadow_density(n_per_volume: float, depth: float, diameter: float, area: float) -> float:

@@ -41,7 +41,7 @@ def same(d1, d2):
                                    atol=1e-6)
 
 
-@pytest.mark.parametrize("shape,seed", [((9, 40, 48), 1), ((16, 64, 64), 2), ((3, 24, 16), 3),
+@pytest.mark.parametrize("shape,seed", [((9, 48, 48), 1), ((16, 64, 64), 2), ((3, 24, 16), 3),
                                         ((1, 32, 32), 4)])
 @pytest.mark.parametrize("min_vox", [0, 5])
 def test_coo_detection_matches_dense_and_oracle(shape, seed, min_vox):
