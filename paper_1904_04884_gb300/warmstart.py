@@ -136,6 +136,87 @@ def train(n_train=256, epochs=8, lr=1e-3, seed0=1, out=DEFAULT_WEIGHTS, spec=SPE
     return net, info
 
 
+def train_stream(seeds=range(1, 10001), init=DEFAULT_WEIGHTS, out=DEFAULT_WEIGHTS, group=16,
+                 lr0=3e-4, lr1=3e-5, eval_seeds=range(20001, 20021),
+                 eval_every=2000, final_eval_seeds=range(20001, 20101), time_limit_s=None,
+                 spec=SPEC, log=print):
+    """Continues training from `init` over fresh samples, each used once: the
+    samples of `seeds` are generated in groups of `group`, their FISTA targets
+    solved together in one batched CUDA graph, then one Adam step per sample
+    (learning rate decaying linearly from lr0 to lr1). Every `eval_every`
+    samples (and before the first) the iterations to F* (1 + 1e-3) from the
+    network's start are measured on `eval_seeds`; at the end on
+    `final_eval_seeds`. Weights go to `out` (and `out` + '.ckpt.npz' at each
+    evaluation); the record to the same name with .json."""
+    from .rihv import Batch
+    dev = torch.device("cuda:0")
+    net = WarmStartUNet.load(init)
+    hs = [handle(spec) for _ in range(group)]
+    batch = Batch(hs)
+    outs = [torch.empty(spec.shape, dtype=torch.complex64, device=dev) for _ in range(group)]
+    h_eval = handle(spec)
+    ref = {}
+
+    def curve(eval_list):
+        rows = []
+        for s in eval_list:
+            if s not in ref:
+                b, hb = make_sample(h_eval, spec, s, dev)
+                fs = reference_objective(h_eval, b, spec)
+                it0, _, _ = iterations_to_tolerance(h_eval, b, spec, None, fs)
+                ref[s] = (b, hb, fs, it0)
+            b, hb, fs, it0 = ref[s]
+            x0 = torch.empty(spec.shape, dtype=torch.complex64, device=dev)
+            net.predict(hb, x0)
+            it1, _, _ = iterations_to_tolerance(h_eval, b, spec, x0, fs)
+            rows.append((s, it0, it1))
+        return {"plain_iters": [r[1] for r in rows], "warm_iters": [r[2] for r in rows],
+                "mean_plain": float(np.mean([r[1] for r in rows])),
+                "mean_warm": float(np.mean([r[2] for r in rows]))}
+
+    seeds = list(seeds)
+    t_start = time.time()
+    record = {"init": os.path.basename(init), "seeds": [seeds[0], seeds[-1]], "group": group,
+              "lr": [lr0, lr1], "target_iters": spec.target_iters, "curve": [], "losses": []}
+    record["curve"].append({"samples": 0, **curve(eval_seeds)})
+    log(json.dumps(record["curve"][-1]))
+    done, loss_acc, loss_n = 0, torch.zeros(1, dtype=torch.float64, device=dev), 0
+    stopped = False
+    for g0 in range(0, len(seeds), group):
+        chunk = seeds[g0:g0 + group]
+        samples = [make_sample(hs[0], spec, s, dev) for s in chunk]
+        holos = [b for b, _ in samples] + [samples[-1][0]] * (group - len(chunk))
+        batch.solve(holos, spec.lam_l1, spec.lam_tv, spec.target_iters, outs)
+        for (b, hb), x in zip(samples, outs):
+            lr = lr0 + (lr1 - lr0) * done / max(1, len(seeds) - 1)
+            loss_acc += net.train_step(hb, (x - net.base_coeff * hb).contiguous(), lr)
+            loss_n += 1
+            done += 1
+        if done % 500 < group:
+            record["losses"].append({"samples": done, "mean_loss": float(loss_acc.item()) / loss_n})
+            loss_acc.zero_()
+            loss_n = 0
+        if done % eval_every < group or done == len(seeds):
+            record["curve"].append({"samples": done, **curve(eval_seeds)})
+            log(json.dumps(record["curve"][-1]))
+            net.save(out + ".ckpt.npz")
+        if time_limit_s and time.time() - t_start > time_limit_s:
+            stopped = True
+            break
+    assert net.errors() == 0, "a convolution kernel's bounded wait gave up"
+    batch.close()
+    record["samples_trained"] = done
+    record["stopped_at_time_limit"] = stopped
+    record["train_seconds"] = time.time() - t_start
+    record["final"] = {"seeds": [min(final_eval_seeds), max(final_eval_seeds)],
+                       **curve(list(final_eval_seeds))}
+    log(json.dumps(record["final"]))
+    net.save(out)
+    with open(os.path.splitext(out)[0] + ".stream.json", "w") as f:
+        json.dump(record, f, indent=1)
+    return record
+
+
 def iterations_to_tolerance(h, b, spec, x0=None, f_star=None, tol=1e-3, max_iters=600):
     """FISTA iterations (checked every 10) until F(x_k) <= F* (1 + tol), and the
     wall time of that solve."""
@@ -187,6 +268,12 @@ def main():
     t.add_argument("--epochs", type=int, default=8)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
+    st = sub.add_parser("stream", help="continue training over fresh samples, each used once")
+    st.add_argument("--first-seed", type=int, default=1)
+    st.add_argument("--n", type=int, default=10000)
+    st.add_argument("--init", default=DEFAULT_WEIGHTS)
+    st.add_argument("--out", required=True)
+    st.add_argument("--time-limit", type=float, default=None)
     e = sub.add_parser("eval")
     e.add_argument("--weights", default=DEFAULT_WEIGHTS)
     e.add_argument("--seeds", type=int, nargs="+", default=[20001, 20002, 20003])
@@ -194,6 +281,10 @@ def main():
         q.add_argument("--lam-l1", type=float, default=SPEC.lam_l1)
         q.add_argument("--lam-tv", type=float, default=SPEC.lam_tv)
     a = p.parse_args()
+    if a.cmd == "stream":
+        train_stream(range(a.first_seed, a.first_seed + a.n), a.init, a.out,
+                     time_limit_s=a.time_limit)
+        return
     spec = SampleSpec(lam_l1=a.lam_l1, lam_tv=a.lam_tv)
     if a.cmd == "train":
         _, info = train(a.n_train, a.epochs, a.lr, out=a.out, spec=spec)
