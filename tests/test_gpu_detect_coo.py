@@ -46,7 +46,8 @@ def same(d1, d2):
 @pytest.mark.parametrize("min_vox", [0, 5])
 def test_coo_detection_matches_dense_and_oracle(shape, seed, min_vox):
     x = blobby(shape, seed)
-    x[shape[0] // 2] = 0                                  # an empty plane
+    if shape[0] > 2:
+        x[shape[0] // 2] = 0                              # an empty plane
     h = handle(shape)
     xd = torch.from_numpy(x).cuda()
     off, rows, cols, vals = h.coo_compact(xd)
