@@ -58,7 +58,8 @@ typedef enum {
 
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
- * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0, tv_zchunk 0. */
+ * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0, tv_zchunk 0,
+ * fft_rows_per_cta 0. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -98,6 +99,10 @@ typedef struct {
                         min(nz, 8) <= tv_zchunk <= 256, capped at nz. Results
                         do not depend on it, except the FISTA restart
                         product's summation order in the fused finalize.    */
+  int fft_rows_per_cta; /* rows transformed per CTA in the row passes of the
+                        register FFT engine (power-of-two nx): 0 (default)
+                        takes 4 or the autotuner's choice; otherwise 2, 4 or
+                        8, dividing ny. Same arithmetic for every value.    */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */
@@ -232,12 +237,14 @@ rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done);
 
 /* Autotuner (not in the paper). Times, on the handle's own scratch, the TV
  * kernel's z-chunk length (8..256 planes per CTA) and steps per launch (1 or
- * 2, i.e. halo depth), and the number of planes each column-pass CTA sums
- * (z-group size), then applies the fastest to the handle. With a non-NULL
+ * 2, i.e. halo depth), the number of planes each column-pass CTA sums
+ * (z-group size), and the row-pass FFT tile (2, 4 or 8 rows per CTA, for
+ * power-of-two nx), then applies the fastest to the handle. With a non-NULL
  * cache_path the result is looked up first (key: nx ny nz tv_dims) and
- * appended after a search, one line per shape. chosen_or_null receives
- * {z-chunk, steps per launch, planes per column group}. Synchronises; the
- * scratch contents (x, y, v) are overwritten. */
+ * appended after a search, one line per shape. chosen_or_null (int[4])
+ * receives {z-chunk, steps per launch, planes per column group, rows per
+ * row-pass CTA}. Synchronises; the scratch contents (x, y, v) are
+ * overwritten. An option tv_zchunk > 0 overrides the tuned z-chunk. */
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_null);
 
 /* Per-plane COO form of a volume (Section 2, GPU implementation paragraph:

@@ -405,12 +405,12 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
 // ---------------------------------------------------------------------------
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 
-template <int N>
+template <int N, int NT = 4>
 struct RShape {
   static constexpr int TT = N / 8;                                  // threads per transform
   static constexpr int NP = ilog2c(N) / 3 + (ilog2c(N) % 3 ? 1 : 0);  // passes
   static constexpr int LDX = N + 4;                                 // exchange row stride
-  static constexpr int kTeams = 4;                                  // transforms per CTA
+  static constexpr int kTeams = NT;                                 // transforms per CTA
   static constexpr int kThreads = kTeams * TT;
   __host__ __device__ static constexpr int radix(int s) {
     return s < ilog2c(N) / 3 ? 8 : (1 << (ilog2c(N) % 3));
@@ -475,10 +475,11 @@ __device__ __forceinline__ void rfft(float2 (&v)[8], int i, float2*& xa, float2*
   }
 }
 
-// Row pass, register engine: four rows of one plane per item (team = row).
-template <bool INV, int IN, int OUT, int EPI, int N>
-__global__ void __launch_bounds__(RShape<N>::kThreads) k_rows_reg(const __grid_constant__ RowArgs a) {
-  using Sh = RShape<N>;
+// Row pass, register engine: NT rows of one plane per item (team = row; 4 by
+// default, 2 or 8 when the autotuner finds them faster for a grid).
+template <bool INV, int IN, int OUT, int EPI, int N, int NT_ = 4>
+__global__ void __launch_bounds__(RShape<N, NT_>::kThreads) k_rows_reg(const __grid_constant__ RowArgs a) {
+  using Sh = RShape<N, NT_>;
   constexpr int TT = Sh::TT, W = kStrip, NT = Sh::kTeams;
   extern __shared__ float2 smem[];
   float2* tw = smem;
@@ -783,10 +784,10 @@ __global__ void __launch_bounds__(kRedThreads) k_zsum_next(const float2* partial
   }
 }
 
-template <bool INV, int IN, int OUT, int EPI, int N>
-cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
-  using Sh = RShape<N>;
-  auto kern = k_rows_reg<INV, IN, OUT, EPI, N>;
+template <bool INV, int IN, int OUT, int EPI, int N, int NT>
+cudaError_t launch_rows_reg_t(const RowArgs& a, cudaStream_t s) {
+  using Sh = RShape<N, NT>;
+  auto kern = k_rows_reg<INV, IN, OUT, EPI, N, NT>;
   const int smem = static_cast<int>(Sh::smem_bytes());
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -800,6 +801,15 @@ cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
   const int grid = items < per_sm * sms ? items : per_sm * sms;
   kern<<<grid, Sh::kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <bool INV, int IN, int OUT, int EPI, int N>
+cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
+  switch (a.teams) {
+    case 2: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 2>(a, s);
+    case 8: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 8>(a, s);
+    default: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 4>(a, s);
+  }
 }
 
 template <int MODE, int N>
@@ -863,8 +873,8 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 // Lengths served by the register engine.
 bool reg_length(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
 
-size_t rows_smem_bytes(int nx) {
-  if (reg_length(nx)) return sizeof(float2) * (nx + 2 * 4 * static_cast<size_t>(nx + 4));
+size_t rows_smem_bytes(int nx, int teams) {
+  if (reg_length(nx)) return sizeof(float2) * (nx + 2 * static_cast<size_t>(teams) * (nx + 4));
   return sizeof(float2) * (2 * static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
 }
 

@@ -107,6 +107,7 @@ struct rihv_ctx {
   int groups = 1, zpg = 1;
   int sms = 152;
   int tv_zchunk = 0;                 // planes per TV z-chunk; 0: tv_default_zchunk
+  int row_teams = 0;                 // rows per CTA of the register row pass; 0: 4
   bool batch_chunks = false;         // being captured into a batched graph (see tv_steps)
   double* fin_partials = nullptr;    // one per CTA of a fused-finalize TV launch
   int fin_ctas = 0;                  // capacity of fin_partials
@@ -169,7 +170,7 @@ struct rihv_batch_st {
   float l1 = -1.f, ltv = -1.f;
   bool warm = false;
   std::vector<rihv_options> opts;
-  std::vector<int> tunes;            // zchunk, zpg per handle
+  std::vector<int> tunes;            // zchunk, zpg, row teams per handle
   std::vector<std::vector<long long>> launches;   // per handle, per stage, per graph launch
   std::vector<int> checks;           // objective checks per handle per launch
   bool conditional = false;          // graph with per-hologram stop tests (IF nodes)
@@ -288,6 +289,7 @@ RowArgs row_args(rihv_ctx* h, const void* src, float2* dst, int nz) {
   a.scale = 1.f;
   a.plan = h->plan_x;
   a.tw = h->tw_x;
+  a.teams = h->opt.fft_rows_per_cta > 0 ? h->opt.fft_rows_per_cta : h->row_teams;
   return a;
 }
 
@@ -709,6 +711,7 @@ void rihv_default_options(rihv_options* o) {
   o->fuse_finalize = 1;
   o->skip_empty_planes = 0;
   o->tv_zchunk = 0;
+  o->fft_rows_per_cta = 0;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -835,7 +838,7 @@ rihv_status rihv_create(int nx, int ny, int nz, double wavelength, double pitch,
   h->tau = any_prop ? 1.0 / (2.0 * nz) : 0.0;
 
   // Kernel smem limits
-  if (rows_smem_bytes(nx) > 227 * 1024 || cols_smem_bytes(COL_FWD_ZSUM, ny) > 227 * 1024)
+  if (rows_smem_bytes(nx, 4) > 227 * 1024 || cols_smem_bytes(COL_FWD_ZSUM, ny) > 227 * 1024)
     return cleanup(fail(h, RIHV_ERR_UNSUPPORTED_SIZE, "shared memory limit"));
   *out = h;
   return RIHV_OK;
@@ -882,7 +885,10 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       (o->tv_steps_per_launch != 1 && o->tv_steps_per_launch != 2) ||
       (o->fuse_finalize != 0 && o->fuse_finalize != 1) ||
       (o->skip_empty_planes != 0 && o->skip_empty_planes != 1) ||
-      (o->tv_zchunk != 0 && (o->tv_zchunk < std::min(8, h->nz) || o->tv_zchunk > kTvMaxChunk)))
+      (o->tv_zchunk != 0 && (o->tv_zchunk < std::min(8, h->nz) || o->tv_zchunk > kTvMaxChunk)) ||
+      (o->fft_rows_per_cta != 0 && o->fft_rows_per_cta != 2 && o->fft_rows_per_cta != 4 &&
+       o->fft_rows_per_cta != 8) ||
+      (o->fft_rows_per_cta != 0 && h->ny % o->fft_rows_per_cta != 0))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   h->opt = *o;
   return RIHV_OK;
@@ -1221,7 +1227,7 @@ static bool same_options(const rihv_options& a, const rihv_options& o) {
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
          a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
          a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes &&
-         a.tv_zchunk == o.tv_zchunk;
+         a.tv_zchunk == o.tv_zchunk && a.fft_rows_per_cta == o.fft_rows_per_cta;
 }
 
 // Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a
@@ -1358,6 +1364,7 @@ static rihv_status batch_capture_cond(rihv_batch b, float l1, float ltv, int ite
     b->opts.push_back(h->opt);
     b->tunes.push_back(h->tv_zchunk);
     b->tunes.push_back(h->zpg);
+    b->tunes.push_back(h->row_teams);
   }
   return RIHV_OK;
 }
@@ -1429,6 +1436,7 @@ static rihv_status batch_capture(rihv_batch b, float l1, float ltv, int iters, b
     b->opts.push_back(h->opt);
     b->tunes.push_back(h->tv_zchunk);
     b->tunes.push_back(h->zpg);
+    b->tunes.push_back(h->row_teams);
   }
   return RIHV_OK;
 }
@@ -1454,8 +1462,8 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
                    b->warm != warm || b->conditional != cond;
   for (int i = 0; i < n && !recapture; ++i) {
     rihv_ctx* h = b->hs[i];
-    recapture = !same_options(b->opts[i], h->opt) || b->tunes[2 * i] != h->tv_zchunk ||
-                b->tunes[2 * i + 1] != h->zpg;
+    recapture = !same_options(b->opts[i], h->opt) || b->tunes[3 * i] != h->tv_zchunk ||
+                b->tunes[3 * i + 1] != h->zpg || b->tunes[3 * i + 2] != h->row_teams;
   }
   // inputs into each handle's own buffers (outside the graph)
   for (int i = 0; i < n; ++i) {
@@ -1528,20 +1536,22 @@ static double time_ms(rihv_ctx* h, const std::function<rihv_status()>& fn, int r
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
   if (!h) return fail(nullptr, RIHV_ERR_INVALID_ARG, "null handle");
   char key[96];
-  snprintf(key, sizeof(key), "rihv-tune-v1 %d %d %d %d", h->nx, h->ny, h->nz, h->opt.tv_dims);
-  int zchunk = -1, per = -1, zpg = -1;
+  snprintf(key, sizeof(key), "rihv-tune-v2 %d %d %d %d", h->nx, h->ny, h->nz, h->opt.tv_dims);
+  int zchunk = -1, per = -1, zpg = -1, teams = -1;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
       char line[256];
       while (fgets(line, sizeof(line), f)) {
-        int a = 0, b2 = 0, c = 0;
+        int a = 0, b2 = 0, c = 0, d = 0;
         const size_t kl = strlen(key);
         if (strncmp(line, key, kl) == 0 && line[kl] == ':' &&
-            sscanf(line + kl + 1, "%d %d %d", &a, &b2, &c) == 3 && a >= 1 && (b2 == 1 || b2 == 2) &&
-            c >= 1 && c <= h->nz && (h->nz + c - 1) / c <= kMaxGroups) {
+            sscanf(line + kl + 1, "%d %d %d %d", &a, &b2, &c, &d) == 4 && a >= 1 &&
+            (b2 == 1 || b2 == 2) && c >= 1 && c <= h->nz && (h->nz + c - 1) / c <= kMaxGroups &&
+            (d == 2 || d == 4 || d == 8) && h->ny % d == 0) {
           zchunk = a;
           per = b2;
           zpg = c;
+          teams = d;
         }
       }
       fclose(f);
@@ -1555,7 +1565,10 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     const int prof = h->prof;
     h->prof = 0;
     const rihv_options saved = h->opt;
+    h->opt.tv_zchunk = 0;          // explicit choices would override the candidates
+    h->opt.fft_rows_per_cta = 0;
     const int saved_zc = h->tv_zchunk, saved_zpg = h->zpg, saved_g = h->groups;
+    const int saved_teams = h->row_teams;
     rihv_status st = RIHV_OK;
     double best = 1e30;
     const int kSteps = 4;
@@ -1602,17 +1615,40 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
         zpg = c;
       }
     }
+    // row-pass tile: transforms per CTA of the register engine (2, 4 or 8
+    // rows), with the chosen column z-groups
+    teams = 4;
+    if (reg_length(h->nx) && st == RIHV_OK) {
+      h->zpg = zpg;
+      h->groups = (h->nz + zpg - 1) / zpg;
+      best = 1e30;
+      for (int t : kRowTeams) {
+        if (h->ny % t != 0 || rows_smem_bytes(h->nx, t) > 227 * 1024) continue;
+        h->row_teams = t;
+        const double ms = time_ms(h, [&] {
+          rihv_status s2 = forward_spectrum(h, h->y, nullptr, h->spec);
+          if (s2 != RIHV_OK) return s2;
+          return adjoint_planes(h, h->spec, h->y, h->v, gs, true);
+        }, 3, &st);
+        if (st != RIHV_OK) break;
+        if (ms < best * 0.99 || (t == 4 && ms < best * 1.01)) {   // 4 unless clearly slower
+          best = ms;
+          teams = t;
+        }
+      }
+    }
     h->opt = saved;
     h->tv_zchunk = saved_zc;
     h->zpg = saved_zpg;
     h->groups = saved_g;
+    h->row_teams = saved_teams;
     h->prof = prof;
     // reset the launch counters the search added
     for (int s = 0; s < kNumStages; ++s) h->stage_launches[s] = 0;
     if (st != RIHV_OK) return st;
     if (cache_path) {
       if (FILE* f = fopen(cache_path, "a")) {
-        fprintf(f, "%s: %d %d %d\n", key, zchunk, per, zpg);
+        fprintf(f, "%s: %d %d %d %d\n", key, zchunk, per, zpg, teams);
         fclose(f);
       }
     }
@@ -1621,10 +1657,12 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
   h->opt.tv_steps_per_launch = per;
   h->zpg = zpg;
   h->groups = (h->nz + zpg - 1) / zpg;
+  h->row_teams = teams;
   if (chosen) {
     chosen[0] = zchunk;
     chosen[1] = per;
     chosen[2] = zpg;
+    chosen[3] = teams;
   }
   return RIHV_OK;
 }

@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
                 ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int),
                 ("fuse_finalize", ctypes.c_int), ("skip_empty_planes", ctypes.c_int),
-                ("tv_zchunk", ctypes.c_int)]
+                ("tv_zchunk", ctypes.c_int), ("fft_rows_per_cta", ctypes.c_int)]
 
 
 class Particle(ctypes.Structure):
@@ -287,10 +287,11 @@ class Rihv:
     coo_expand = rihv_coo_expand
 
     def rihv_autotune(self, cache_path=None):
-        """Times the TV z-chunk / steps per launch and the column-pass z-groups on
-        this handle and applies the fastest; returns (z_chunk, steps_per_launch,
-        planes_per_group). With cache_path the result is looked up / stored."""
-        out = (ctypes.c_int * 3)()
+        """Times the TV z-chunk / steps per launch, the column-pass z-groups and
+        the row-pass FFT tile (rows per CTA) on this handle and applies the
+        fastest; returns (z_chunk, steps_per_launch, planes_per_group,
+        rows_per_cta). With cache_path the result is looked up / stored."""
+        out = (ctypes.c_int * 4)()
         path = cache_path.encode() if cache_path else None
         self._check(self.L.rihv_autotune(self.h, path, out), self.h)
         return tuple(out)

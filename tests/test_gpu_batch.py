@@ -123,12 +123,13 @@ def test_autotune_choice_is_valid_cached_and_correct(tmp_path):
     op = O.Optics(nx=96, ny=64, nz=40, wavelength=532e-9, pitch=5e-6, z0=5e-3, dz=50e-6)
     cache = str(tmp_path / "tune.txt")
     h = _handle(op)
-    zc, per, zpg = h.autotune(cache)
+    zc, per, zpg, rows = h.autotune(cache)
     assert zc in (8, 16, 32, 64, 128) and per in (1, 2) and 1 <= zpg <= op.nz
-    assert os.path.exists(cache) and open(cache).read().count("rihv-tune-v1 96 64 40 3") == 1
+    assert rows == 4                                       # nx = 96: shared-memory engine
+    assert os.path.exists(cache) and open(cache).read().count("rihv-tune-v2 96 64 40 3") == 1
     h2 = _handle(op)
-    assert h2.autotune(cache) == (zc, per, zpg)           # loaded, not searched again
-    assert open(cache).read().count("rihv-tune-v1") == 1
+    assert h2.autotune(cache) == (zc, per, zpg, rows)     # loaded, not searched again
+    assert open(cache).read().count("rihv-tune-v2") == 1
     # the tuned handle still matches the oracle
     v = synth.random_complex(synth.Stream(5), op.shape)
     out = torch.empty(op.shape, dtype=torch.complex64, device="cuda:0")
@@ -138,5 +139,19 @@ def test_autotune_choice_is_valid_cached_and_correct(tmp_path):
     x = synth.random_complex(synth.Stream(6), op.shape)
     y = torch.empty((op.ny, op.nx), dtype=torch.complex64, device="cuda:0")
     h2.forward(torch.from_numpy(x.astype(np.complex64)).cuda(), y)
+    ref = O.forward(x, op)
+    assert np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_autotune_row_tile_on_power_of_two_grid(tmp_path):
+    """On a power-of-two grid the tuner also picks the row-pass tile (2, 4 or
+    8 rows per CTA); the tuned handle's solve matches the untuned one."""
+    op = O.Optics(nx=256, ny=128, nz=24, wavelength=532e-9, pitch=5e-6, z0=5e-3, dz=50e-6)
+    h = _handle(op)
+    zc, per, zpg, rows = h.autotune(str(tmp_path / "tune.txt"))
+    assert rows in (2, 4, 8)
+    x = synth.random_complex(synth.Stream(7), op.shape)
+    y = torch.empty((op.ny, op.nx), dtype=torch.complex64, device="cuda:0")
+    h.forward(torch.from_numpy(x.astype(np.complex64)).cuda(), y)
     ref = O.forward(x, op)
     assert np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5

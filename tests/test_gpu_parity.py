@@ -69,6 +69,25 @@ def test_adjoint_parity(nx, ny, nz):
     assert rel_l2(out.cpu().numpy(), O.adjoint(r, op)) <= OP_TOL
 
 
+@pytest.mark.parametrize("rows", [2, 4, 8])
+@pytest.mark.parametrize("nx,ny,nz", [(128, 64, 5), (1024, 16, 2), (64, 256, 9)])
+def test_row_tile_shapes_match_oracle(nx, ny, nz, rows):
+    """Every row-pass tile of the register FFT engine (2, 4 or 8 rows per CTA)
+    gives the forward and the adjoint to the operator tolerance."""
+    op = optics(nx, ny, nz)
+    h = handle(op)
+    h.set_options(fft_rows_per_cta=rows)
+    x = synth.random_complex(synth.Stream(nx + ny + rows), op.shape)
+    out = torch.empty((ny, nx), dtype=torch.complex64, device=dev())
+    h.forward(to_dev(x), out)
+    r = synth.random_complex(synth.Stream(nx * ny + rows), (ny, nx))
+    vol = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+    h.adjoint(to_dev(r), vol)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), O.forward(x, op)) <= OP_TOL
+    assert rel_l2(vol.cpu().numpy(), O.adjoint(r, op)) <= OP_TOL
+
+
 def test_evanescent_band_parity():
     op = optics(32, 32, 3, wl=632.8e-9, pitch=0.4e-6, z0=2e-6, dz=1e-6)
     x = synth.random_complex(synth.Stream(5), op.shape)
