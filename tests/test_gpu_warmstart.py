@@ -1,7 +1,9 @@
 """What the trained warm start gains: on held-out seeds (training used seeds
 1-1536), FISTA started from the network's prediction reaches the objective
 tolerance F* (1 + 1e-3) in fewer iterations than FISTA from zero, where F* is
-the objective of a 600-iteration plain solve, and finds the same particles.
+the objective of a 600-iteration plain solve, and its detections differ from
+the plain solution's only where the two solutions' |x| can fall on either
+side of the threshold.
 The same holds when the warm starts are solved together as one batched CUDA
 graph, whose results equal the individual warm solves bit for bit."""
 import numpy as np
@@ -66,31 +68,6 @@ def test_warm_and_plain_detections_agree(cases):
               f"band 1e-3 max|x|: exempt {r3['exempt']}, differing {len(r3['bad'])}")
         assert r["bad"] == [], (c["seed"], r["bad"][:10])
         assert r["matched"] > 0
-
-
-def _found(dets, parts, tol_xy=2.0, tol_z=5.0):
-    """Indices of the placed discs with a detection within 2 pixels laterally
-    and 5 planes axially (disc centres are continuous, pixel i spans
-    [i, i + 1); centroids are voxel indices)."""
-    from scipy.spatial import cKDTree
-    c = np.array([d["centroid"] for d in dets], np.float64).reshape(-1, 3)
-    t = np.stack([parts.x - 0.5, parts.y - 0.5, parts.z.astype(np.float64)], axis=1)
-    scale = np.array([1.0 / tol_xy, 1.0 / tol_xy, 1.0 / tol_z])
-    d, _ = cKDTree(c * scale).query(t * scale, p=np.inf)
-    return set(np.nonzero(d <= 1.0)[0].tolist())
-
-
-def test_warm_and_plain_find_the_same_particles(cases):
-    """Particle level: the placed discs that the warm solution's detections
-    find are those the plain solution's find (the noise and twin-image
-    fragments the weak weights leave around them are what differs)."""
-    for c in cases:
-        parts, _ = W.discs(W.SPEC, c["seed"])
-        fp, fw = _found(c["det_plain"], parts), _found(c["det_warm"], parts)
-        both = len(fp & fw)
-        print(f"seed {c['seed']}: discs {len(parts)}, found plain {len(fp)} warm {len(fw)} "
-              f"both {both}")
-        assert both >= 0.95 * max(len(fp), len(fw)), (c["seed"], len(fp), len(fw), both)
 
 
 def test_batched_warm_starts_reach_the_tolerance(cases):
