@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--workload", default="fista_large_1024x1024x256",
                    help="named workload of the timed step (default: the 1024x1024x256 case)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the library's default tiles instead of running its autotuner")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the secondary measurements (mid workload, time to tolerance, "
                         "mixed-size sequence)")
@@ -456,6 +458,13 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     h = Rihv(*w.optics_tuple(), stream=stream)
     h.set_options(tv_dims=w.tv_dims, n_inner=w.n_inner, check_every=10)
+    tuned = None
+    if not args.no_autotune:
+        # the library's autotuner on this handle (before any timing): TV z-chunk and
+        # steps per launch, column-pass z-groups, row-pass FFT tile
+        zc, per_l, zpg, rows = h.autotune()
+        tuned = {"tv_zchunk": zc, "tv_steps_per_launch": per_l, "col_planes_per_group": zpg,
+                 "fft_rows_per_cta": rows}
 
     b = rank_hologram(make_hologram(w, h, torch, dev), w, rank)
     b_dev = torch.from_numpy(b).to(dev)
@@ -530,7 +539,7 @@ def main():
     # the first launch of a prox (p = 0: read v, write p), 64 for the last
     # launch with the fused finalize (read v, p, x_{k-1}, y_k; write x_k and
     # y_{k+1} instead of p).
-    per = h.options.tv_steps_per_launch
+    per = tuned["tv_steps_per_launch"] if tuned else h.options.tv_steps_per_launch
     tv_kernel = "k_tv_step2" if per == 2 else "k_tv_step"
     peak, peak_kind = hbm_peak()
     kinds = {}
@@ -589,7 +598,8 @@ def main():
                    "tv_inner_steps": w.n_inner, "tv_dims": w.tv_dims,
                    "step": "full FISTA solve + objective every 10 iters + detection",
                    "l2": f"inputs larger than L2 ({8 * w.nvox / 1e6:.0f} MB per volume)",
-                   "detections": ndet, "parallelism": f"replicas x{world}"},
+                   "detections": ndet, "parallelism": f"replicas x{world}",
+                   "tuned": tuned},
         "e2e": {"value": e2e_value, "unit": "voxel-iter/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(w.nx * w.ny * 4),
                 "d2h_bytes_per_step": int(w.nvox * 8 + (w.iters // 10) * 8)},
