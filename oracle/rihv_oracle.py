@@ -51,6 +51,22 @@ R11 Detection (Section 2, last paragraphs; Section 3.2 parameters): |x| above
     is taken in float32 (|x|^2 = re*re + im*im, each operation rounded to
     float32; threshold^2 = (rel*rel) * max|x|^2 in float32) so that it is the
     same decision the float32 GPU kernel takes.
+R12 FASTA-style solver (Section 2 says its solver follows the FASTA
+    implementation and names none of its options): forward-backward splitting x_{k+1} = prox_{tau_k g}(x_k -
+    tau_k grad f(x_k)) with the adaptive spectral (Barzilai-Borwein) step of
+    Goldstein, Studer and Baraniuk (steepest-descent step tau_s = <dx,dx>/<dx,dg>,
+    minimum-residual step tau_m = <dx,dg>/<dg,dg>; tau = tau_m if 2 tau_m >
+    tau_s, else tau_s - tau_m/2; 1.5 times the previous step when <dx,dg> <= 0)
+    and their non-monotone backtracking: accept when f(x_{k+1}) <= max of the
+    last 10 values of f + Re<dx, grad f(x_k)> + ||dx||^2 / (2 tau), up to a
+    rounding slack of 1e-6 times that maximum (the bound is met with equality
+    whenever dx lies in the top eigenspace of H^H H at tau = 1/L_f), otherwise
+    halve tau and retry (at most 20 times). First step 1/L_f. Inner products
+    over C^n are the real inner product of R^2n. No acceleration.
+R13 Accelerated TV dual (FGP, Beck-Teboulle's fast gradient projection, the
+    accelerated form of R8): p_k = Pi(r_k + D(v - mu D^H r_k)/(4 dims mu)),
+    t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2, r_{k+1} = p_k + ((t_k - 1)/t_{k+1})
+    (p_k - p_{k-1}), r_1 = p_0 = 0, t_1 = 1; x = v - mu D^H p_K.
 """
 from __future__ import annotations
 
@@ -248,11 +264,37 @@ def tv_prox_gp(v: np.ndarray, mu: float, n_inner: int, dims: int = 3,
     return (x, (px, py, pz)) if return_dual else x
 
 
+def tv_prox_fgp(v: np.ndarray, mu: float, n_inner: int, dims: int = 3,
+                return_dual: bool = False):
+    """prox_{mu TV}(v) by the accelerated dual iteration (FGP; R13): the
+    gradient-projection step of R8 taken at the extrapolated dual r_k."""
+    v = np.asarray(v, dtype=np.complex128)
+    p_prev = [np.zeros_like(v) for _ in range(3)]
+    r = [np.zeros_like(v) for _ in range(3)]
+    if mu == 0.0 or n_inner == 0:
+        return (v.copy(), tuple(p_prev)) if return_dual else v.copy()
+    step = 1.0 / (4.0 * dims * mu)
+    t = 1.0
+    p = p_prev
+    for _ in range(n_inner):
+        u = v - mu * grad_op_adjoint(*r, dims)
+        gx, gy, gz = grad_op(u, dims)
+        p = list(project_unit_ball(r[0] + step * gx, r[1] + step * gy, r[2] + step * gz))
+        t_next = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        beta = (t - 1.0) / t_next
+        r = [pc + beta * (pc - pp) for pc, pp in zip(p, p_prev)]
+        p_prev, t = p, t_next
+    x = v - mu * grad_op_adjoint(*p, dims)
+    return (x, tuple(p)) if return_dual else x
+
+
 def prox_fused_lasso(v: np.ndarray, t_l1: float, t_tv: float, n_inner: int,
-                     dims: int = 3) -> np.ndarray:
+                     dims: int = 3, fgp: bool = False) -> np.ndarray:
     """Fused-lasso prox = soft threshold of the TV prox (Section 2, FL paragraph;
-    R9). ``t_l1`` and ``t_tv`` are already multiplied by the step tau."""
-    return soft_threshold(tv_prox_gp(v, t_tv, n_inner, dims), t_l1)
+    R9). ``t_l1`` and ``t_tv`` are already multiplied by the step tau. With
+    ``fgp`` the TV prox runs the accelerated dual iteration (R13)."""
+    tv = tv_prox_fgp if fgp else tv_prox_gp
+    return soft_threshold(tv(v, t_tv, n_inner, dims), t_l1)
 
 
 def objective(x: np.ndarray, b: np.ndarray, optics: Optics, lam_l1: float,
@@ -300,6 +342,50 @@ def fista(b: np.ndarray, optics: Optics, lam_l1: float, lam_tv: float, iters: in
         if check_every and k % check_every == 0:
             trace.append((k, objective(x, b, optics, lam_l1, lam_tv, dims)))
     return x, trace
+
+
+def fasta(b: np.ndarray, optics: Optics, lam_l1: float, lam_tv: float, iters: int,
+          n_inner: int, dims: int = 3, x0: np.ndarray | None = None, window: int = 10,
+          shrink: float = 0.5, max_backtracks: int = 20, fgp: bool = False,
+          check_every: int = 0):
+    """Forward-backward splitting with the adaptive spectral step and
+    non-monotone backtracking (R12). Returns (x_final, trace, info): trace
+    lists (iteration, F(x_k)) every ``check_every`` iterations; info holds the
+    accepted steps tau_k and the number of backtracks."""
+    tau = 1.0 / lipschitz(optics)
+    x = (np.zeros(optics.shape, np.complex128) if x0 is None
+         else np.asarray(x0, np.complex128).copy())
+    f_hist = [data_term(x, b, optics)]
+    g = grad_data(x, b, optics)
+    trace, taus, backtracks = [], [], 0
+    for k in range(1, iters + 1):
+        for _ in range(max_backtracks + 1):
+            x_new = prox_fused_lasso(x - tau * g, tau * lam_l1, tau * lam_tv, n_inner, dims, fgp)
+            dx = x_new - x
+            f_new = data_term(x_new, b, optics)
+            f_max = max(f_hist[-window:])
+            bound = (f_max + float(np.vdot(dx, g).real)
+                     + float(np.vdot(dx, dx).real) / (2.0 * tau))
+            if f_new <= bound + 1e-6 * abs(f_max):
+                break
+            tau *= shrink
+            backtracks += 1
+        taus.append(tau)
+        g_new = grad_data(x_new, b, optics)
+        dg = g_new - g
+        dxdg = float(np.vdot(dx, dg).real)
+        if dxdg > 0.0:
+            tau_s = float(np.vdot(dx, dx).real) / dxdg
+            tau_m = dxdg / float(np.vdot(dg, dg).real)
+            tau_next = tau_m if 2.0 * tau_m > tau_s else tau_s - 0.5 * tau_m
+        else:
+            tau_next = 0.0
+        tau = tau_next if (tau_next > 0.0 and np.isfinite(tau_next)) else 1.5 * tau
+        x, g = x_new, g_new
+        f_hist.append(f_new)
+        if check_every and k % check_every == 0:
+            trace.append((k, objective(x, b, optics, lam_l1, lam_tv, dims)))
+    return x, trace, {"taus": taus, "backtracks": backtracks}
 
 
 # --------------------------------------------------------------------------

@@ -173,3 +173,30 @@ def fista_three_sequence(grad, prox, tau, x0, iters, restart=False):
         x_prev = x
         xs.append(x)
     return xs
+
+
+def project_c3(q):
+    """Per-voxel projection of a stacked dual q [3][...] onto |q|_2 <= 1 in C^3."""
+    nrm = np.sqrt((np.abs(q) ** 2).sum(axis=0))
+    return q / np.maximum(1.0, nrm)
+
+
+def tv_dual_fista(v, mu, iters, dims=3):
+    """The accelerated TV dual written as plain FISTA (three-sequence form
+    above) on min_q 1/2 ||v - mu D^H q||^2 over |q| <= 1, with D the sparse
+    difference matrices: gradient -mu D (v - mu D^H q), step 1/(mu^2 4 dims)
+    (the bound 4 dims on ||D||^2), projection as the prox. Returns the duals
+    q_1 ... q_iters, each stacked [3][nz][ny][nx]."""
+    shape = v.shape
+    mats = grad_matrices(shape, dims)
+    vv = np.asarray(v, np.complex128).ravel()
+
+    def dh(q):
+        return sum(m.conj().T @ c.ravel() for m, c in zip(mats, q))
+
+    def grad(q):
+        u = vv - mu * dh(q)
+        return np.stack([-(mu * (m @ u)).reshape(shape) for m in mats])
+
+    return fista_three_sequence(grad, project_c3, 1.0 / (mu * mu * 4.0 * dims),
+                                np.zeros((3,) + shape, np.complex128), iters)

@@ -169,3 +169,69 @@ def test_fista_iterates_by_hand():
     assert np.abs(x3.imag).max() == 0.0
     # the momentum moved the third iterate
     assert np.abs(step(h2) - h3).max() > 1e-3
+
+
+def test_fasta_on_the_identity_keeps_the_step_and_the_closed_form():
+    """H = I: the gradient step with tau = 1/L = 1/2 gives v = b whatever the
+    iterate, so every iterate is prox(b), dx = 0 after the first step and the
+    gradient change is 2 dx: the steepest-descent and minimum-residual steps
+    are both 1/2, the adaptive rule keeps 1/2 for the second step, and nothing
+    backtracks. A rule off by any factor (tau_s + tau_m, tau_m / 2, ...) moves
+    the second iterate away from prox(b). (At the fixed point dx = 0 and the
+    rule's fallback, 1.5 times the step, takes over.)"""
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal((IDENT.ny, IDENT.nx))
+    lam1, lamtv = 0.3, 0.2
+    ref = O.prox_fused_lasso(b[None].astype(complex), lam1 / 2, lamtv / 2, 200, 3)
+    x1, _, info1 = O.fasta(b, IDENT, lam1, lamtv, iters=1, n_inner=200)
+    np.testing.assert_allclose(x1, ref, atol=1e-13)
+    x, _, info = O.fasta(b, IDENT, lam1, lamtv, iters=2, n_inner=200)
+    np.testing.assert_allclose(x, ref, atol=1e-13)
+    assert info["backtracks"] == 0 and np.allclose(info["taus"], [0.5, 0.5], rtol=1e-14)
+
+
+def test_fasta_steps_on_two_coincident_planes_by_hand():
+    """Two planes at z = 0: H x = x_0 + x_1, so H^H H x = (s, s) with
+    s = x_0 + x_1, L = 2 ||H||^2 = 4. For any step, dg = 2 H^H H dx gives
+    <dx, dg> = 2 ||ds||^2 and ||dg||^2 = 8 ||ds||^2 (ds = dx_0 + dx_1): the
+    minimum-residual step is always 1/4 and the steepest-descent step is
+    ||dx||^2 / (2 ||ds||^2). Each accepted step after the first must be 1/4
+    when 1/2 > tau_s, else tau_s - 1/8 (or a backtracked fraction of it)."""
+    op = O.Optics(nx=8, ny=4, nz=2, wavelength=632.8e-9, pitch=10e-6, z0=0.0, dz=0.0)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal((4, 8))
+    x0 = rng.standard_normal((2, 4, 8)) + 1j * rng.standard_normal((2, 4, 8))
+    lam = 0.3
+    xs = [x0.astype(complex)]
+    taus = []
+    for k in range(1, 9):
+        x, _, info = O.fasta(b, op, lam, 0.0, iters=k, n_inner=0, x0=x0)
+        xs.append(x)
+        taus = info["taus"]
+    assert taus[0] == 0.25
+    checked = 0
+    for k in range(1, 8):
+        dx = xs[k] - xs[k - 1]
+        ds = dx[0] + dx[1]
+        if np.vdot(ds, ds).real < 1e-12 * np.vdot(dx, dx).real:
+            continue
+        tau_s = np.vdot(dx, dx).real / (2 * np.vdot(ds, ds).real)
+        expect = 0.25 if 0.5 > tau_s else tau_s - 0.125
+        # the step used for x_{k+1} is the rule's value, or that halved by backtracking
+        ratio = taus[k] / expect
+        assert abs(ratio - 2.0 ** np.round(np.log2(ratio))) < 1e-9 and ratio <= 1 + 1e-12, k
+        checked += 1
+    assert checked >= 5 and max(taus) > 1.0      # both branches of the rule taken
+
+
+def test_fasta_reaches_the_lasso_minimiser():
+    """With lam_tv = 0, FASTA's limit satisfies the lasso's optimality
+    conditions, like FISTA's (same problem as the KKT pin above)."""
+    b = _hologram(SMALL, 2)
+    lam = 0.5
+    x, _, info = O.fasta(b, SMALL, lam, 0.0, iters=1500, n_inner=0)
+    g = O.grad_data(x, b, SMALL)
+    on = np.abs(x) > 1e-9
+    assert on.sum() > 0
+    np.testing.assert_allclose(g[on], -lam * x[on] / np.abs(x[on]), atol=2e-6)
+    assert np.abs(g[~on]).max() <= lam * (1 + 1e-6)

@@ -190,3 +190,30 @@ def test_gp_projection_by_hand():
         # the corner has no backward neighbours: D^H p there is -(p_x + p_y)
         dh00 = -(px[0, 0, 0] + py[0, 0, 0])
         np.testing.assert_allclose(x[0, 0, 0], w[0, 0, 0] - 0.5 * dh00, atol=1e-14)
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_fgp_duals_match_plain_fista_on_the_dual(dims):
+    """The oracle's accelerated dual iteration (FGP) equals FISTA, written
+    independently in three-sequence form with sparse-matrix operators, applied
+    to the TV dual problem: the duals after 1, 2, 5 and 12 steps to 1e-12,
+    and the resulting prox."""
+    v = _rand((4, 6, 5), 31)
+    mu = 0.2
+    qs = B.tv_dual_fista(v, mu, 12, dims)
+    for k in (1, 2, 5, 12):
+        x, p = O.tv_prox_fgp(v, mu, k, dims, return_dual=True)
+        q = qs[k - 1]
+        for c in range(3 if dims == 3 else 2):
+            np.testing.assert_allclose(p[c], q[c], atol=1e-12)
+    # acceleration changes the iterates from the plain gradient projection
+    assert np.linalg.norm(O.tv_prox_fgp(v, mu, 5, dims) - O.tv_prox_gp(v, mu, 5, dims)) > 1e-6
+
+
+def test_fgp_converges_to_the_certified_prox():
+    v = _rand((4, 5, 6), 32)
+    mu = 0.15
+    x, p = O.tv_prox_fgp(v, mu, 3000, 3, return_dual=True)
+    assert B.tv_prox_gap(x, p, v, mu) < 1e-12
+    x_gp = O.tv_prox_gp(v, mu, 6000, 3)
+    assert np.linalg.norm(x - x_gp) < 1e-6 * np.linalg.norm(x)
