@@ -59,7 +59,7 @@ typedef enum {
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
  * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0, tv_zchunk 0,
- * fft_rows_per_cta 0. */
+ * fft_rows_per_cta 0, tv_fgp 0, solver 0. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -103,6 +103,20 @@ typedef struct {
                         register FFT engine (power-of-two nx): 0 (default)
                         takes 4 or the autotuner's choice; otherwise 2, 4 or
                         8, dividing ny. Same arithmetic for every value.    */
+  int tv_fgp;        /* 1: the TV prox runs the accelerated dual iteration
+                        (Beck-Teboulle's fast gradient projection: each step
+                        taken at r_k = p_{k-1} + ((t_{k-1} - 1)/t_k)(p_{k-1} -
+                        p_{k-2})), one step per launch, separate finalize;
+                        the first use allocates three more dual volumes'
+                        worth of scratch (6 x 8 B per voxel). 0 (default):
+                        gradient projection (Section 2, TV prox paragraph).  */
+  int solver;        /* 0 (default): FISTA with gradient restart (Section 2,
+                        FISTA paragraph). 1: forward-backward splitting with
+                        FASTA's adaptive spectral step and non-monotone
+                        backtracking (window 10, step halved on a failed
+                        test, at most 20 times; first step 1/L); its host
+                        loop synchronises twice per iteration, and the first
+                        use allocates two gradient volumes and a candidate.  */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */
@@ -246,6 +260,15 @@ rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done);
  * row-pass CTA}. Synchronises; the scratch contents (x, y, v) are
  * overwritten. An option tv_zchunk > 0 overrides the tuned z-chunk. */
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_null);
+
+/* Steps of the last rihv_solve run with the FASTA-style solver (option
+ * solver = 1; not in the paper beyond its naming FASTA): the accepted step
+ * size of every iteration, in order, into taus (host, first `capacity`
+ * written), their number into *n_steps, and the number of backtracking
+ * halvings into *backtracks (may be NULL). After a FISTA solve *n_steps is
+ * that of the last FASTA solve on the handle (0 if none). */
+rihv_status rihv_fasta_steps(rihv_handle h, double* taus, int capacity, int* n_steps,
+                             int* backtracks);
 
 /* Per-plane COO form of a volume (Section 2, GPU implementation paragraph:
  * volumes stored in the coordinate sparse format, every plane indexing its

@@ -61,7 +61,8 @@ R12 FASTA-style solver (Section 2 says its solver follows the FASTA
     last 10 values of f + Re<dx, grad f(x_k)> + ||dx||^2 / (2 tau), up to a
     rounding slack of 1e-6 times that maximum (the bound is met with equality
     whenever dx lies in the top eigenspace of H^H H at tau = 1/L_f), otherwise
-    halve tau and retry (at most 20 times). First step 1/L_f. Inner products
+    halve tau and retry (at most 20 times, the last candidate then being
+    taken). First step 1/L_f. Inner products
     over C^n are the real inner product of R^2n. No acceleration.
 R13 Accelerated TV dual (FGP, Beck-Teboulle's fast gradient projection, the
     accelerated form of R8): p_k = Pi(r_k + D(v - mu D^H r_k)/(4 dims mu)),
@@ -312,7 +313,7 @@ def objective(x: np.ndarray, b: np.ndarray, optics: Optics, lam_l1: float,
 def fista(b: np.ndarray, optics: Optics, lam_l1: float, lam_tv: float, iters: int,
           n_inner: int, dims: int = 3, restart: bool = True,
           accelerate: bool = True, x0: np.ndarray | None = None,
-          check_every: int = 0):
+          check_every: int = 0, fgp: bool = False):
     """Fused-lasso FISTA. Returns (x_final, trace) where trace lists
     (iteration, F(x_k)) every ``check_every`` iterations (and none if 0).
 
@@ -328,7 +329,7 @@ def fista(b: np.ndarray, optics: Optics, lam_l1: float, lam_tv: float, iters: in
     x = x_prev
     for k in range(1, iters + 1):
         v = y - tau * grad_data(y, b, optics)
-        x = prox_fused_lasso(v, tau * lam_l1, tau * lam_tv, n_inner, dims)
+        x = prox_fused_lasso(v, tau * lam_l1, tau * lam_tv, n_inner, dims, fgp)
         if accelerate:
             t_next = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
             y_next = x + ((t - 1.0) / t_next) * (x - x_prev)
@@ -359,14 +360,14 @@ def fasta(b: np.ndarray, optics: Optics, lam_l1: float, lam_tv: float, iters: in
     g = grad_data(x, b, optics)
     trace, taus, backtracks = [], [], 0
     for k in range(1, iters + 1):
-        for _ in range(max_backtracks + 1):
+        for attempt in range(max_backtracks + 1):
             x_new = prox_fused_lasso(x - tau * g, tau * lam_l1, tau * lam_tv, n_inner, dims, fgp)
             dx = x_new - x
             f_new = data_term(x_new, b, optics)
             f_max = max(f_hist[-window:])
             bound = (f_max + float(np.vdot(dx, g).real)
                      + float(np.vdot(dx, dx).real) / (2.0 * tau))
-            if f_new <= bound + 1e-6 * abs(f_max):
+            if f_new <= bound + 1e-6 * abs(f_max) or attempt == max_backtracks:
                 break
             tau *= shrink
             backtracks += 1

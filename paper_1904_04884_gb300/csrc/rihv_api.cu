@@ -131,6 +131,13 @@ struct rihv_ctx {
   float2* v = nullptr;
   float2* pa[3] = {nullptr, nullptr, nullptr};
   float2* pb[3] = {nullptr, nullptr, nullptr};
+  float2* pc[3] = {nullptr, nullptr, nullptr};   // accelerated dual: p_k, p_{k-1} (allocated on use)
+  float2* pd[3] = {nullptr, nullptr, nullptr};
+  float2* fasta_g[2] = {nullptr, nullptr};      // FASTA: gradients at x_k and at the candidate
+  float2* fasta_x = nullptr;                    // FASTA: candidate x_{k+1}
+  double* fasta_dots = nullptr;                 // FASTA: inner products of the last test
+  std::vector<double> fasta_taus;               // FASTA: accepted steps of the last solve
+  int fasta_backtracks = 0;
   DevScalars* sc = nullptr;
   RedWork red{};
   double* trace = nullptr;     // device objective trace
@@ -397,11 +404,53 @@ int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = 
   return best;
 }
 
+// K steps of the accelerated dual (FGP), one per launch: the step at the
+// extrapolated dual r_k (held in pa / pb, read by TMA) writes p_k (pc / pd)
+// and r_{k+1}; t_k and the extrapolation factors are computed here in FP64.
+// Returns the buffer set holding p_K.
+rihv_status tv_steps_fgp(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal) {
+  if (!h->pc[0]) return fail(h, RIHV_ERR_INVALID_ARG, "accelerated dual scratch not allocated");
+  StageScope sc(h, ST_TV, k);
+  TvArgs a{};
+  CK(make_volume_tmap(&a.tm_v, v, h->nx, h->ny, h->nz, kTvBoxH1, kTvBoxW));
+  a.err = h->tv_err;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.dims = h->opt.tv_dims;
+  a.zchunk = h->opt.tv_zchunk > 0 ? std::min(h->opt.tv_zchunk, h->nz) : 32;
+  a.mu = mu;
+  a.step = 1.f / (4.f * a.dims * mu);
+  float2** ps[2] = {h->pc, h->pd};
+  bool src_is_b = true;
+  double t = 1.0;
+  for (int i = 0; i < k; ++i) {
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+    a.fgp_beta = static_cast<float>((t - 1.0) / tn);
+    t = tn;
+    float2** rdst = src_is_b ? h->pa : h->pb;
+    for (int c = 0; c < 3; ++c) {
+      a.tm_p[c] = src_is_b ? h->tm_pb[0][c] : h->tm_pa[0][c];
+      a.pout[c] = ps[i & 1][c];
+      a.pprev[c] = i > 0 ? ps[(i - 1) & 1][c] : nullptr;
+      a.rout[c] = i + 1 < k ? rdst[c] : nullptr;
+    }
+    {
+      StageScope sub(h, i == 0 ? ST_TV_FIRST : ST_TV_MID, 1, 2);
+      CK(launch_tv_step(i == 0, 1, a, h->stream, false, true));
+    }
+    src_is_b = !src_is_b;
+  }
+  *pfinal = ps[(k - 1) & 1];
+  return RIHV_OK;
+}
+
 // K dual steps; returns the buffer set holding the final p. With `fin` (two
 // steps per launch, K >= 2) the last launch also runs the finalize and
 // *pfinal is null.
 rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* const** pfinal,
                      const FinArgs* fin = nullptr, int fin_mode = FIN_PROX) {
+  if (h->opt.tv_fgp) return tv_steps_fgp(h, v, mu, k, pfinal);
   // With tv_steps_per_launch = 2, two dual steps per launch; an odd K starts
   // with a single-step launch, so that the last launch is always a pair.
   const int per = h->opt.tv_steps_per_launch;
@@ -680,6 +729,101 @@ rihv_status emit_particles(rihv_ctx* h, int ncomp, int min_vox, rihv_particle* o
   return RIHV_OK;
 }
 
+// Forward-backward splitting with FASTA's adaptive spectral step and
+// non-monotone backtracking (the option solver = 1). The hologram is in
+// h->holo and, if warm, x_0 in h->x. Per iteration: v = x_k - tau g_k, the
+// fused-lasso prox of v (step tau) into the candidate, its forward (data term
+// f and residual spectrum), then Re<dx, g_k> and ||dx||^2 on the device; the
+// host accepts the candidate when f <= max of the last 10 f + Re<dx, g_k> +
+// ||dx||^2 / (2 tau) (up to 1e-6 of that maximum) or halves tau and retries
+// (at most 20 times). After acceptance g_{k+1} = 2 H^H r_{k+1} and the next
+// step from <dx, dg>, ||dx||^2, ||dg||^2: tau_m = <dx,dg>/||dg||^2, tau_s =
+// ||dx||^2/<dx,dg>, tau = tau_m if 2 tau_m > tau_s else tau_s - tau_m/2, or
+// 1.5 tau when <dx,dg> <= 0. Two host synchronisations per iteration.
+rihv_status solve_fasta(rihv_ctx* h, bool warm, float l1, float ltv, int iters, int* check_out,
+                        int* done_out) {
+  if (!h->fasta_g[0]) return fail(h, RIHV_ERR_INVALID_ARG, "FASTA scratch not allocated");
+  const size_t vb = h->nvox * sizeof(float2);
+  const float gscale = static_cast<float>(2.0 / static_cast<double>(h->nxy));
+  CKS(fft2_plane(h, h->holo, true, h->bhat));
+  if (!warm) CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
+  CK(launch_init_scalars(h->sc, 0, 0, h->stream));
+  CK(cudaMemsetAsync(h->tv_err, 0, sizeof(int), h->stream));
+  int cur = 0;
+  CKS(forward_spectrum(h, h->x, h->bhat, h->spec));
+  CKS(adjoint_planes(h, h->spec, nullptr, h->fasta_g[cur], gscale, false));
+  DevScalars hs{};
+  CK(cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<double> f_hist = {hs.rnorm2};
+  double tau = h->tau;
+  h->fasta_taus.clear();
+  h->fasta_backtracks = 0;
+  const int M = h->opt.check_every;
+  const bool stop_test = h->opt.f_star > 0.0 && M > 0;
+  int check = 0, done = 0;
+  double dots[3];
+  for (int k = 1; k <= iters; ++k) {
+    double f_new = 0.0;
+    for (int bt = 0;; ++bt) {
+      CK(launch_grad_step(h->x, h->fasta_g[cur], static_cast<float>(tau), h->v, h->nvox, h->stream));
+      CKS(prox_into(h, h->v, static_cast<float>(tau) * l1, static_cast<float>(tau) * ltv,
+                    h->opt.n_inner, FIN_PROX, h->fasta_x));
+      CKS(forward_spectrum(h, h->fasta_x, h->bhat, h->spec));
+      CK(launch_dots(h->fasta_x, h->x, h->fasta_g[cur], nullptr, h->nvox, h->red, h->fasta_dots,
+                     h->stream));
+      CK(cudaMemcpyAsync(dots, h->fasta_dots, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaMemcpyAsync(&hs, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      f_new = hs.rnorm2;
+      if (!std::isfinite(f_new) || !std::isfinite(dots[0]) || !std::isfinite(dots[1]))
+        return fail(h, RIHV_ERR_NONFINITE, "FASTA step produced NaN or Inf");
+      const size_t w0 = f_hist.size() > 10 ? f_hist.size() - 10 : 0;
+      const double f_max = *std::max_element(f_hist.begin() + w0, f_hist.end());
+      const double bound = f_max + dots[0] + dots[1] / (2.0 * tau);
+      if (f_new <= bound + 1e-6 * std::fabs(f_max) || bt == 20) break;
+      tau *= 0.5;
+      ++h->fasta_backtracks;
+    }
+    h->fasta_taus.push_back(tau);
+    const int nxt = cur ^ 1;
+    CKS(adjoint_planes(h, h->spec, nullptr, h->fasta_g[nxt], gscale, false));
+    CK(launch_dots(h->fasta_x, h->x, h->fasta_g[nxt], h->fasta_g[cur], h->nvox, h->red,
+                   h->fasta_dots, h->stream));
+    CK(cudaMemcpyAsync(dots, h->fasta_dots, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double tau_next = 0.0;
+    if (dots[0] > 0.0) {
+      const double tau_s = dots[1] / dots[0];
+      const double tau_m = dots[0] / dots[2];
+      tau_next = (2.0 * tau_m > tau_s) ? tau_m : tau_s - 0.5 * tau_m;
+    }
+    tau = (tau_next > 0.0 && std::isfinite(tau_next)) ? tau_next : 1.5 * tau;
+    std::swap(h->x, h->fasta_x);
+    cur = nxt;
+    f_hist.push_back(f_new);
+    done = k;
+    if (M > 0 && k % M == 0) {
+      // the data term of x_k is the last forward's (sc->rnorm2)
+      CK(launch_objective(h->x, h->nx, h->ny, h->nz, h->opt.tv_dims, l1, ltv, h->sc, h->red,
+                          h->trace + check, h->stream));
+      ++check;
+      if (stop_test) {
+        double f = 0;
+        CK(cudaMemcpyAsync(&f, h->trace + check - 1, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (f <= h->opt.f_star * (1.0 + h->opt.tol)) break;
+      }
+    }
+  }
+  *check_out = check;
+  *done_out = done;
+  return RIHV_OK;
+}
+
 // After the stream has finished: TV wait failures and non-finite reductions.
 rihv_status read_solve_errors(rihv_ctx* h) {
   DevScalars hs{};
@@ -712,6 +856,8 @@ void rihv_default_options(rihv_options* o) {
   o->skip_empty_planes = 0;
   o->tv_zchunk = 0;
   o->fft_rows_per_cta = 0;
+  o->tv_fgp = 0;
+  o->solver = 0;
 }
 
 const char* rihv_last_error(rihv_handle h) {
@@ -888,8 +1034,22 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       (o->tv_zchunk != 0 && (o->tv_zchunk < std::min(8, h->nz) || o->tv_zchunk > kTvMaxChunk)) ||
       (o->fft_rows_per_cta != 0 && o->fft_rows_per_cta != 2 && o->fft_rows_per_cta != 4 &&
        o->fft_rows_per_cta != 8) ||
-      (o->fft_rows_per_cta != 0 && h->ny % o->fft_rows_per_cta != 0))
+      (o->fft_rows_per_cta != 0 && h->ny % o->fft_rows_per_cta != 0) ||
+      (o->tv_fgp != 0 && o->tv_fgp != 1) || (o->solver != 0 && o->solver != 1))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
+  // scratch of the optional iterations is allocated here, not inside a solve
+  // (which may be being captured into a graph)
+  if (o->tv_fgp && !h->pc[0])
+    for (int c = 0; c < 3; ++c) {
+      CKS(dalloc(h, &h->pc[c], h->nvox));
+      CKS(dalloc(h, &h->pd[c], h->nvox));
+    }
+  if (o->solver == 1 && !h->fasta_g[0]) {
+    CKS(dalloc(h, &h->fasta_g[0], h->nvox));
+    CKS(dalloc(h, &h->fasta_g[1], h->nvox));
+    CKS(dalloc(h, &h->fasta_x, h->nvox));
+    CKS(dalloc(h, &h->fasta_dots, 4));
+  }
   h->opt = *o;
   return RIHV_OK;
 }
@@ -958,10 +1118,13 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
 
   CKS(copy_in(h, h->holo, hologram, h->nxy * sizeof(float)));
   if (x0) CKS(copy_in(h, h->x, x0, vb));
-  CKS(enqueue_setup(h, x0 != nullptr));
   int done = 0;
   int check = 0;
-  for (int k = 1; k <= iters; ++k) {
+  if (h->opt.solver == 1)
+    CKS(solve_fasta(h, x0 != nullptr, lambda_l1, lambda_tv, iters, &check, &done));
+  else
+    CKS(enqueue_setup(h, x0 != nullptr));
+  for (int k = 1; k <= iters && h->opt.solver == 0; ++k) {
     const int before = check;
     CKS(enqueue_iteration(h, k, lambda_l1, lambda_tv, &check));
     done = k;
@@ -978,6 +1141,17 @@ rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, fl
   CK(cudaStreamSynchronize(h->stream));
   if (iters_done) *iters_done = done;
   return read_solve_errors(h);
+}
+
+rihv_status rihv_fasta_steps(rihv_handle h, double* taus, int capacity, int* n_steps,
+                             int* backtracks) {
+  if (!h || !n_steps || capacity < 0 || (capacity > 0 && !taus))
+    return fail(h, RIHV_ERR_INVALID_ARG, "invalid arguments");
+  const int n = static_cast<int>(h->fasta_taus.size());
+  for (int i = 0; i < n && i < capacity; ++i) taus[i] = h->fasta_taus[i];
+  *n_steps = n;
+  if (backtracks) *backtracks = h->fasta_backtracks;
+  return RIHV_OK;
 }
 
 rihv_status rihv_coo_compact(rihv_handle h, const void* x, long long* plane_offsets, int* rows,
@@ -1227,7 +1401,8 @@ static bool same_options(const rihv_options& a, const rihv_options& o) {
          a.n_inner == o.n_inner && a.check_every == o.check_every &&
          a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
          a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes &&
-         a.tv_zchunk == o.tv_zchunk && a.fft_rows_per_cta == o.fft_rows_per_cta;
+         a.tv_zchunk == o.tv_zchunk && a.fft_rows_per_cta == o.fft_rows_per_cta &&
+         a.tv_fgp == o.tv_fgp && a.solver == o.solver;
 }
 
 // Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a
@@ -1455,6 +1630,10 @@ rihv_status rihv_batch_solve(rihv_batch b, const float* const* holograms, float 
     const int M = h->opt.check_every;
     CKS(ensure_trace(h, (M > 0) ? iters / M : 0));
   }
+  for (auto* h : b->hs)
+    if (h->opt.solver != 0)
+      return fail(h, RIHV_ERR_INVALID_ARG, "the FASTA solver decides its steps on the host; "
+                                          "batched graphs run FISTA only");
   bool cond = false;   // some hologram has a stop test: graph with IF nodes
   for (auto* h : b->hs) cond = cond || (h->opt.f_star > 0.0 && h->opt.check_every > 0);
   const bool warm = x0s != nullptr;
@@ -1567,6 +1746,7 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     const rihv_options saved = h->opt;
     h->opt.tv_zchunk = 0;          // explicit choices would override the candidates
     h->opt.fft_rows_per_cta = 0;
+    h->opt.tv_fgp = 0;
     const int saved_zc = h->tv_zchunk, saved_zpg = h->zpg, saved_g = h->groups;
     const int saved_teams = h->row_teams;
     rihv_status st = RIHV_OK;

@@ -177,11 +177,18 @@ struct TvArgs {
   int* occ;               // FISTA: [nz + 1], zeroed before the launch; occ[z] set for
                           // every plane z with a non-zero voxel of x_k or y_{k+1},
                           // occ[nz] = 1 if some plane has none; or null
+  // Accelerated dual (FGP), one-step launches: the input dual (tm_p) is the
+  // extrapolated r_k, pout receives p_k = Pi(r_k + step D u); pprev holds
+  // p_{k-1} (not read on the first step, where it is zero); when rout[0] is
+  // non-null it receives r_{k+1} = p_k + fgp_beta (p_k - p_{k-1}).
+  const float2* pprev[3];
+  float2* rout[3];
+  float fgp_beta;
 };
 // nsteps = 1 or 2 dual steps in one launch; first: the input dual is zero;
 // final (two-step launches only): fused finalize, no dual output.
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s,
-                           bool final = false);
+                           bool final = false, bool fgp = false);
 // Box of box_rows x box_cols complex elements: (kTvBoxH1, kTvBoxW) for the
 // one-step kernel, (kTv2BoxH, kTv2BoxW) for the two-step kernel.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,
@@ -211,6 +218,17 @@ cudaError_t launch_objective(const float2* x, int nx, int ny, int nz, int dims, 
                              cudaStream_t s);
 cudaError_t launch_wait_selftest(int* flag, int polls, cudaStream_t s);
 cudaError_t launch_init_scalars(DevScalars* sc, int accelerate, int restart, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// FASTA-style solver (fasta_kernels.cu)
+// ---------------------------------------------------------------------------
+// v = x - tau g over n complex values.
+cudaError_t launch_grad_step(const float2* x, const float2* g, float tau, float2* v, size_t n,
+                             cudaStream_t s);
+// out[0] = Re<a - b, c - d>, out[1] = ||a - b||^2, out[2] = ||c - d||^2 (d null: 0),
+// FP64 on the device; uses partial rows 1-3 and ticket 4 of w.
+cudaError_t launch_dots(const float2* a, const float2* b, const float2* c, const float2* d,
+                        size_t n, RedWork w, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Detection (detect_kernels.cu)

@@ -188,8 +188,10 @@ struct TvLayout1 {   // one dual step per launch
   static constexpr int kBytes = kBarOffset + NSTAGE * 8;
 };
 
-// One dual gradient-projection step (used for an odd step count).
-template <bool FIRST>
+// One dual gradient-projection step (used for an odd step count). FGP: the
+// step of the accelerated dual, which also writes the extrapolated dual for
+// the next step (see TvArgs).
+template <bool FIRST, bool FGP = false>
 __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ TvArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float2(*U)[R1Y][R1X] = reinterpret_cast<float2(*)[R1Y][R1X]>(smem + NSTAGE * 4 * SLOT1);
@@ -267,6 +269,20 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_step(const __grid_constant__ 
       a.pout[0][gidx] = qx;
       a.pout[1][gidx] = qy;
       if (a.dims == 3) a.pout[2][gidx] = qz;
+      if (FGP && a.rout[0]) {
+        // r_{k+1} = p_k + beta (p_k - p_{k-1}), p_0 = 0
+        float2 ox = make_float2(0.f, 0.f), oy = ox, oz = ox;
+        if (!FIRST) {
+          ox = a.pprev[0][gidx];
+          oy = a.pprev[1][gidx];
+          if (a.dims == 3) oz = a.pprev[2][gidx];
+        }
+        const float bt = a.fgp_beta;
+        a.rout[0][gidx] = make_float2(qx.x + bt * (qx.x - ox.x), qx.y + bt * (qx.y - ox.y));
+        a.rout[1][gidx] = make_float2(qy.x + bt * (qy.x - oy.x), qy.y + bt * (qy.y - oy.y));
+        if (a.dims == 3)
+          a.rout[2][gidx] = make_float2(qz.x + bt * (qz.x - oz.x), qz.y + bt * (qz.y - oz.y));
+      }
     }
     __syncthreads();
   }
@@ -966,9 +982,11 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
-cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s, bool final) {
+cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s, bool final,
+                           bool fgp) {
   if (nsteps == 2 && (a.nx & 1)) return cudaErrorInvalidValue;   // pairs of x positions
   if (final && nsteps != 2) return cudaErrorInvalidValue;
+  if (fgp && nsteps != 1) return cudaErrorInvalidValue;
   const int tx = nsteps == 2 ? (final ? kTv2TxF : TX2) : TX;
   const int ty = nsteps == 2 ? (final ? kTv2TyF : kTv2Ty) : TY;
   dim3 grid((a.nx + tx - 1) / tx, (a.ny + ty - 1) / ty, (a.nz + a.zchunk - 1) / a.zchunk);
@@ -980,7 +998,8 @@ cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t
                                                       : k_tv_step2<false, true, FIN_FISTA>))
                                     : (first ? k_tv_step2<true, true> : k_tv_step2<false, true>))
                            : (first ? k_tv_step2<true, false> : k_tv_step2<false, false>))
-                  : (first ? k_tv_step<true> : k_tv_step<false>);
+                  : (fgp ? (first ? k_tv_step<true, true> : k_tv_step<false, true>)
+                         : (first ? k_tv_step<true> : k_tv_step<false>));
   const int bytes = nsteps == 2 ? (final ? TvLayout2<kTv2WarpsF>::kBytes : TvLayout2<kTv2Warps>::kBytes)
                                 : TvLayout1::kBytes;
   const int threads = nsteps == 2 ? 32 * (final ? kTv2WarpsF : kTv2Warps) : kTvThreads;

@@ -23,7 +23,7 @@ STATUS = {0: "RIHV_OK", 1: "RIHV_ERR_INVALID_ARG", 2: "RIHV_ERR_CUDA", 3: "RIHV_
 
 EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stream",
            "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
-           "rihv_solve", "rihv_detect", "rihv_detect_coo", "rihv_set_profiling", "rihv_stage_times",
+           "rihv_solve", "rihv_detect", "rihv_detect_coo", "rihv_fasta_steps", "rihv_set_profiling", "rihv_stage_times",
            "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
            "rihv_batch_destroy", "rihv_autotune"]
 
@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
                 ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int),
                 ("fuse_finalize", ctypes.c_int), ("skip_empty_planes", ctypes.c_int),
-                ("tv_zchunk", ctypes.c_int), ("fft_rows_per_cta", ctypes.c_int)]
+                ("tv_zchunk", ctypes.c_int), ("fft_rows_per_cta", ctypes.c_int),
+                ("tv_fgp", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class Particle(ctypes.Structure):
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_detect": (i, [H, vp, f, i, ctypes.POINTER(Particle), i, ctypes.POINTER(i)]),
         "rihv_detect_coo": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, f, i,
                                 ctypes.POINTER(Particle), i, ctypes.POINTER(i)]),
+        "rihv_fasta_steps": (i, [H, ctypes.POINTER(d), i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "rihv_set_profiling": (i, [H, i]),
         "rihv_stage_times": (i, [H, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "rihv_step_size": (i, [H, ctypes.POINTER(d)]),
@@ -282,6 +284,17 @@ class Rihv:
             _ptr(vals, device=True, dtype="complex64", name="vals") if n else None, n,
             _ptr(x_out, device=True, dtype="complex64", numel=self.nvox, name="x_out")), self.h)
 
+    def rihv_fasta_steps(self):
+        """(accepted step sizes, backtracking halvings) of the last FASTA solve."""
+        n, bt = ctypes.c_int(), ctypes.c_int()
+        self._check(self.L.rihv_fasta_steps(self.h, None, 0, ctypes.byref(n), ctypes.byref(bt)),
+                    self.h)
+        arr = (ctypes.c_double * max(1, n.value))()
+        self._check(self.L.rihv_fasta_steps(self.h, arr, n.value, ctypes.byref(n),
+                                            ctypes.byref(bt)), self.h)
+        return list(arr[:n.value]), bt.value
+
+    fasta_steps = rihv_fasta_steps
     detect_coo = rihv_detect_coo
     coo_compact = rihv_coo_compact
     coo_expand = rihv_coo_expand
