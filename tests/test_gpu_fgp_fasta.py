@@ -40,12 +40,12 @@ def test_fgp_prox_matches_oracle(nx, ny, nz, k, dims):
     v = synth.random_complex(synth.Stream(nz * 5 + k + dims), op.shape)
     h = handle(op, tv_dims=dims, tv_fgp=1)
     out = torch.empty(op.shape, dtype=torch.complex64, device="cuda:0")
-    h.prox_fused_lasso(torch.from_numpy(v.astype(np.complex64)).cuda(), 0.3, 0.05, k, out)
+    h.prox_fused_lasso(torch.from_numpy(v.astype(np.complex64)).cuda(), 0.3, 0.5, k, out)
     torch.cuda.synchronize()
-    ref = O.prox_fused_lasso(v, 0.3, 0.05, k, dims, fgp=True)
+    ref = O.prox_fused_lasso(v, 0.3, 0.5, k, dims, fgp=True)
     assert rel_l2(out.cpu().numpy(), ref) <= OP_TOL
-    if k > 2:      # the accelerated dual differs from the plain one
-        assert rel_l2(ref, O.prox_fused_lasso(v, 0.3, 0.05, k, dims)) > 10 * OP_TOL
+    if k > 2:      # from the third step on, the accelerated dual differs from the plain one
+        assert rel_l2(ref, O.prox_fused_lasso(v, 0.3, 0.5, k, dims)) > 100 * OP_TOL
 
 
 def _tiny():
@@ -95,9 +95,12 @@ def test_fasta_stop_test_and_batch_refusal():
     x = torch.empty(op.shape, dtype=torch.complex64, device="cuda:0")
     tr = np.zeros(8)
     h.solve(b, w.lam_l1, w.lam_tv, 40, x, trace=tr)
-    h.set_options(n_inner=w.n_inner, check_every=5, solver=1, f_star=float(tr[-1]), tol=1e-2)
+    # the method is not monotone (the objective jumps after long steps), so the
+    # stop threshold is 10 % above the last value: met first at iteration 10
+    h.set_options(n_inner=w.n_inner, check_every=5, solver=1, f_star=float(tr[-1]), tol=0.1)
     tr2 = np.zeros(8)
     done = h.solve(b, w.lam_l1, w.lam_tv, 40, x, trace=tr2)
-    assert done < 40 and done % 5 == 0 and tr2[done // 5 - 1] <= tr[-1] * 1.01
+    first = next(5 * (i + 1) for i, f in enumerate(tr) if f <= tr[-1] * 1.1)
+    assert done == first < 40 and tr2[done // 5 - 1] <= tr[-1] * 1.1
     with pytest.raises(RihvError):
         Batch([h]).solve([b], w.lam_l1, w.lam_tv, 10, [x])
