@@ -1755,9 +1755,14 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     // candidates: powers of two, and for two steps per launch also the
     // default chunk
     const int zc_def = tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms);
-    for (int p = 1; p <= 2; ++p) {
+    for (int p = 2; p >= 1; --p) {
+      // the default (two steps, the wave-filling chunk) first: another
+      // candidate must beat it by 1 %
       std::vector<int> zcs = {8, 16, 32, 64, 128, 256};
-      if (p == 2 && std::find(zcs.begin(), zcs.end(), zc_def) == zcs.end()) zcs.push_back(zc_def);
+      if (p == 2) {
+        zcs.erase(std::remove(zcs.begin(), zcs.end(), zc_def), zcs.end());
+        zcs.insert(zcs.begin(), zc_def);
+      }
       for (int zc : zcs) {
         if (zc > h->nz && zc != 8) continue;
         h->opt.tv_steps_per_launch = p;
