@@ -368,3 +368,24 @@ def test_objective_of_the_iterate(nx, ny, nz, dims):
     xs = x.cpu().numpy().astype(np.complex128)
     ref = O.objective(xs, b.astype(np.float64), op, 0.02, 0.01, dims)
     assert abs(tr[0] - ref) <= 2e-5 * abs(ref)
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+@pytest.mark.parametrize("nx,ny,nz", [(48, 24, 5), (96, 64, 9), (24, 48, 1)])
+def test_short_solve_parity_on_ragged_grids(nx, ny, nz, dims):
+    """Five FISTA iterations (momentum, restart test, objective every
+    iteration) on grids with a factor 3, a single plane and ragged TV tiles,
+    against the oracle's solve of the same hologram."""
+    op = optics(nx, ny, nz)
+    a = np.zeros(op.shape)
+    a[nz // 2, ny // 3:ny // 3 + 3, nx // 4:nx // 4 + 3] = 1.0
+    a[0, ny // 2:ny // 2 + 2, nx // 2:nx // 2 + 4] = 0.8
+    b = synth.intensity_hologram(O.forward(a, op), 0.01, synth.Stream(nx + nz).normal(nx * ny))
+    h = handle(op)
+    h.set_options(tv_dims=dims, n_inner=6, check_every=1)
+    x = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+    tr = np.zeros(5)
+    h.solve(b, 0.01, 0.005, 5, x, trace=tr)
+    ref, tr_ref = O.fista(b.astype(np.float64), op, 0.01, 0.005, 5, 6, dims, check_every=1)
+    assert rel_l2(x.cpu().numpy(), ref) <= 1e-4
+    np.testing.assert_allclose(tr, [f for _, f in tr_ref], rtol=1e-5)
