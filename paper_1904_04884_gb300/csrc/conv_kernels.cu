@@ -18,14 +18,17 @@
 // (warp w owns lanes 32w..32w+31), adds the bias, applies ReLU and stores
 // BF16 or FP32.
 //
-// Weight gradient (K = voxels, split over CTAs):
-//   D[m][n] = sum_v A[m][v] B[n][v],  m = tap*C_in + c,  n = c_out
-//   A[m][v] = X[v + off_tap][c],  B[n][v] = dY[v][n]
-// Both operands are MN-major here (for a fixed voxel the channels are
-// contiguous in memory), staged as 8 (voxel) x 16-byte (8 channel) core
-// matrices (SBO = 128 B along M/N, LBO along K). Each CTA accumulates 128 rows
-// over its voxel range and writes FP32 partials that a second kernel sums in a
-// fixed order.
+// Weight gradient (K = voxels, on the same halo tiles):
+//   D_tap[o][c] = sum_v dY[v][o] X[v + off_tap][c]
+// A CTA owns one 16-channel input chunk and a run of 128 x 2 voxel tiles.
+// Per tile, TMA stages the output gradient [o/8][row][x][8] and the input
+// halo of the chunk, double buffered. Both operands are MN-major (for a fixed
+// voxel the channels are contiguous): A = dY with M = c_out (rows beyond c_out
+// read other shared memory; their results are never read), B = the halo with
+// N = 16 channels, and the B operand of tap (dz, dy, dx) is again only a
+// descriptor offset into the halo. Each tap accumulates in its own 16 TMEM
+// columns (27 x 16 = 432 of 512) over all of the CTA's tiles; the epilogue
+// writes FP32 partials per CTA that a second kernel sums in a fixed order.
 //
 // All waits are bounded: on timeout the CTA records an error, waits (bounded)
 // for its issued MMAs, releases its tensor memory and exits.
@@ -41,7 +44,6 @@ namespace {
 constexpr int kM = 128;                // voxels per CTA tile (MMA M)
 constexpr int kThreads = 128;
 constexpr int kWaitLimit = 1 << 22;
-constexpr int kWgK = 64;               // voxels per weight-gradient K stage
 
 // ---- PTX helpers -----------------------------------------------------------
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -318,130 +320,147 @@ __global__ void __launch_bounds__(kThreads) k_conv_tile(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
-// Weight-gradient kernel: grid (m tiles, voxel splits)
+// Weight-gradient kernel: grid (splits, input-channel chunks of 16)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_conv_wgrad(const __grid_constant__ WgradArgs a) {
+constexpr int kWgGyBytes = 8 * kConvTH * kConvTW * 16;      // 8 groups of c_out (<= 64)
+constexpr int kWgStage = kWgGyBytes + kConvHaloBytes;       // gy, then the 16-channel halo
+constexpr int kWgSmem = 128 + 2 * kWgStage;
+// A descriptors span 16 c_out groups (M = 128) from each stage's gy base
+static_assert(128 + kWgStage + 16 * (kWgGyBytes / 8) <= kWgSmem, "wgrad A span exceeds smem");
+static_assert(kWgStage % 128 == 0 && kWgGyBytes % 128 == 0, "TMA destinations 128-byte aligned");
+constexpr int kWgCols = 512;                                // TMEM columns (27 x 16 used)
+
+struct WgradMaps {
+  CUtensorMap x[kConvMaxGroups];   // per 8-channel group of the input, halo box
+  CUtensorMap gy[8];               // per 8-channel group of the output gradient, tile box
+};
+
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad_tile(const __grid_constant__ WgradArgs a,
+                                                               const __grid_constant__ WgradMaps maps) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int cin = a.cin, n = a.cout;
-  const int ng = n / 8;
-  const uint32_t a_bytes = kM * kWgK * 2;   // 16 KB
-  const uint32_t b_bytes = n * kWgK * 2;
+  // bars: 0-1 tile loaded (per stage), 2-3 MMAs of the stage done
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
-  unsigned char* stage0 = smem + 128;
-  unsigned char* sa[2] = {stage0, stage0 + a_bytes + b_bytes};
-  unsigned char* sb[2] = {stage0 + a_bytes, stage0 + 2 * a_bytes + b_bytes};
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 64);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tmem_cols(n);
+  const int og = a.cout / 8;
+  const int chunk = blockIdx.y;                        // input channels 16 chunk ..
+  const int tx = (a.w + kConvTW - 1) / kConvTW, ty = (a.h + kConvTH - 1) / kConvTH;
+  const long ntiles = static_cast<long>(tx) * ty * a.d;
+  const long t0 = static_cast<long>(blockIdx.x) * a.tiles_per_split;
+  const long t1 = t0 + a.tiles_per_split < ntiles ? t0 + a.tiles_per_split : ntiles;
+  const int n = t1 > t0 ? static_cast<int>(t1 - t0) : 0;
+  const uint32_t tx_bytes = static_cast<uint32_t>(og) * (kWgGyBytes / 8) + kConvHaloBytes;
 
   if (tid == 0) {
-    mbar_init(saddr(&bars[0]), 1);
-    mbar_init(saddr(&bars[1]), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(saddr(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(saddr(tmem_slot), ncols);
+  if (warp == 0) tmem_alloc(saddr(tmem_slot), kWgCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = mma_idesc(kM, 16, 1, 1);
+  const uint32_t base = saddr(smem + 128);
 
-  const size_t nvox = static_cast<size_t>(a.d) * a.h * a.w;
-  const int m0 = blockIdx.x * kM;
-  const int mtot = 27 * cin;
-  const size_t v0 = static_cast<size_t>(blockIdx.y) * a.vox_per_split;
-  const size_t v1 = v0 + a.vox_per_split < nvox ? v0 + a.vox_per_split : nvox;
-  const int nstages = static_cast<int>((v1 > v0 ? v1 - v0 : 0) + kWgK - 1) / kWgK;
-  const uint32_t idesc = mma_idesc(kM, n, 1, 1);
+  // tile i of this CTA -> (x0, y0, z), loaded into stage s
+  auto issue = [&](int i, int st) {
+    const long t = t0 + i;
+    const int xt = static_cast<int>(t % tx);
+    const long r = t / tx;
+    const int y0 = static_cast<int>(r % ty) * kConvTH, z = static_cast<int>(r / ty);
+    const int x0 = xt * kConvTW;
+    const uint32_t sb = base + st * kWgStage;
+    const uint32_t bar = saddr(&bars[st]);
+    mbar_expect_tx(bar, tx_bytes);
+    for (int g = 0; g < og; ++g)
+      tma_load_4d(sb + g * (kWgGyBytes / 8), &maps.gy[g], 0, x0, y0, z, bar);
+    for (int j = 0; j < 2; ++j)
+      tma_load_4d(sb + kWgGyBytes + j * kConvHaloKu, &maps.x[2 * chunk + j], 0, x0 - 1, y0 - 1,
+                  z - 1, bar);
+  };
+
   bool ok = true;
-  int issued = -1;
-
-  for (int st = 0; st < nstages && ok; ++st) {
-    const int buf = st & 1;
-    if (st >= 2) {
-      const bool w_ok = mbar_wait(saddr(&bars[buf]), ((st - 2) >> 1) & 1);
-      ok = __syncthreads_and(w_ok) != 0;
+  int loaded_wait = -1;    // last tile whose load was waited for
+  int issued = -1;         // last tile whose load was issued
+  int committed = -1;      // last tile whose MMAs were committed
+  if (tid == 0 && n > 0) {
+    issue(0, 0);
+    issued = 0;
+    for (int i = 0; i < n && ok; ++i) {
+      const int st = i & 1;
+      ok = mbar_wait(saddr(&bars[st]), (i >> 1) & 1);
       if (!ok) break;
-    }
-    const size_t vs = v0 + static_cast<size_t>(st) * kWgK;
-    // A: 8 voxel groups x 16 channel groups x 8 voxels, unit = 8 channels
-    for (int u = tid; u < (kWgK / 8) * 16 * 8; u += kThreads) {
-      const int r = u & 7, mg = (u >> 3) & 15, kg = u >> 7;
-      const size_t vv = vs + kg * 8 + r;
-      const int m = m0 + mg * 8;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (vv < v1 && m < mtot) {
-        const int t = m / cin, c = m - t * cin;
+      loaded_wait = i;
+      tc_fence_after();
+      const uint32_t sg = base + st * kWgStage;
+      const uint32_t sh = sg + kWgGyBytes;
+      for (int t = 0; t < 27; ++t) {
         int dz, dy, dx;
         tap_offset(t, dz, dy, dx);
-        const int x = static_cast<int>(vv % a.w) + dx;
-        const int y = static_cast<int>((vv / a.w) % a.h) + dy;
-        const int z = static_cast<int>(vv / (static_cast<size_t>(a.w) * a.h)) + dz;
-        if (z >= 0 && z < a.d && y >= 0 && y < a.h && x >= 0 && x < a.w)
-          val = __ldg(reinterpret_cast<const uint4*>(
-              a.x + ((static_cast<size_t>(z) * a.h + y) * a.w + x) * cin + c));
+        for (int mt = 0; mt < kConvTH; ++mt) {
+          for (int k = 0; k < kConvTW / 16; ++k) {
+            const uint64_t ad = smem_desc(sg + mt * (kConvTW * 16) + k * 256, 128, kWgGyBytes / 8);
+            const uint32_t hoff = (((dz + 1) * (kConvTH + 2) + mt + dy + 1) * kConvHX + 16 * k + dx + 1) * 16;
+            const uint64_t bd = smem_desc(sh + hoff, 128, kConvHaloKu);
+            umma_bf16(tmem + t * 16, ad, bd, idesc, (i > 0 || mt > 0 || k > 0) ? 1u : 0u);
+          }
+        }
       }
-      *reinterpret_cast<uint4*>(sa[buf] + (kg * 16 + mg) * 128 + r * 16) = val;
+      umma_commit(saddr(&bars[2 + st]));
+      committed = i;
+      if (i + 1 < n) {
+        // the other stage held tile i - 1: its MMAs must be done before reuse
+        if (i >= 1) {
+          ok = mbar_wait(saddr(&bars[2 + (st ^ 1)]), ((i - 1) >> 1) & 1);
+          if (!ok) break;
+        }
+        issue(i + 1, st ^ 1);
+        issued = i + 1;
+      }
     }
-    // B: dY rows of these voxels
-    for (int u = tid; u < (kWgK / 8) * ng * 8; u += kThreads) {
-      const int r = u & 7, gq = (u >> 3) % ng, kg = (u >> 3) / ng;
-      const size_t vv = vs + kg * 8 + r;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (vv < v1) val = __ldg(reinterpret_cast<const uint4*>(a.gy + vv * n + gq * 8));
-      *reinterpret_cast<uint4*>(sb[buf] + (kg * ng + gq) * 128 + r * 16) = val;
+    if (ok && committed >= 0) ok = mbar_wait(saddr(&bars[2 + (committed & 1)]), (committed >> 1) & 1);
+    if (!ok) {
+      atomicExch(a.err, 1);
+      // bounded drains: loads in flight, then the last commit
+      for (int i = loaded_wait + 1; i <= issued; ++i) mbar_wait(saddr(&bars[i & 1]), (i >> 1) & 1);
+      if (committed >= 0) mbar_wait(saddr(&bars[2 + (committed & 1)]), (committed >> 1) & 1);
     }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = saddr(sa[buf]), b0 = saddr(sb[buf]);
-      for (int s = 0; s < kWgK / 16; ++s)
-        umma_bf16(tmem, smem_desc(a0 + s * 2 * 2048, 2048, 128),
-                  smem_desc(b0 + s * 2 * ng * 128, ng * 128, 128), idesc, (st > 0 || s > 0) ? 1u : 0u);
-      umma_commit(saddr(&bars[buf]));
-    }
-    issued = st;
   }
-  if (issued >= 0) {
-    const bool w_ok = mbar_wait(saddr(&bars[issued & 1]), (issued >> 1) & 1);
-    ok = (__syncthreads_and(w_ok) != 0) && ok;
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, ncols);
-    return;
-  }
+  tc_fence_before();
+  ok = __syncthreads_and(tid != 0 || ok) != 0;
   tc_fence_after();
-  const int row = warp * 32 + lane;
-  float* dst = a.partial + (static_cast<size_t>(blockIdx.y) * gridDim.x * kM + m0 + row) * n;
-  for (int c0 = 0; c0 < n; c0 += 8) {
-    float acc[8];
-    if (issued >= 0) {
-      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, acc);
-    } else {
+  if (ok) {
+    // warp w reads TMEM lanes 32w..32w+31 (c_out row o); 27 x 16 columns
+    const int o = warp * 32 + lane;
+    const int cin = a.cin;
+    float* dst = a.partial + (static_cast<size_t>(blockIdx.x) * a.cout + o) * 27 * cin + chunk * 16;
+    for (int col = 0; col < 27 * 16; col += 8) {
+      float acc[8];
+      if (n > 0) {
+        tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col, acc);
+      } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+      }
+      if (o < a.cout) {
+        const int t = col / 16, c = col % 16;
+        float4* d4 = reinterpret_cast<float4*>(dst + t * cin + c);
+        d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
     }
-    float4* d4 = reinterpret_cast<float4*>(dst + c0);
-    d4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    d4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, ncols);
+  if (warp == 0) tmem_dealloc(tmem, kWgCols);
 }
 
-// gW[o][t][c] = sum over splits of partial[split][t*cin + c][o] (fixed order)
-__global__ void k_wgrad_reduce(const float* partial, int nsplit, int mpad, int cin, int cout,
-                               float* gw) {
-  const int total = cout * 27 * cin;
+// gW[i] = sum over splits of partial[split][i], i = (o * 27 + t) * cin + c (fixed order)
+__global__ void k_wgrad_reduce(const float* partial, int nsplit, int total, float* gw) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int o = i / (27 * cin);
-    const int m = i - o * 27 * cin;   // t*cin + c
     float s = 0.f;
-    for (int sp = 0; sp < nsplit; ++sp) s += partial[(static_cast<size_t>(sp) * mpad + m) * cout + o];
+    for (int sp = 0; sp < nsplit; ++sp) s += partial[static_cast<size_t>(sp) * total + i];
     gw[i] = s;
   }
 }
@@ -452,8 +471,6 @@ size_t conv_smem_bytes(int ck, int n) {
   (void)ck;
   return 128 + kConvHaloBytes + 2 * 9 * static_cast<size_t>(n) * 32;
 }
-size_t wgrad_smem_bytes(int cout) { return 128 + 2 * (static_cast<size_t>(kM) * kWgK * 2 + cout * kWgK * 2); }
-
 cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s) {
   // one 4D tensor map per 8-channel group of the gathered input:
   // dims (8 channels, x, y, z), box (8, 130, kTH + 2, 3), zero fill
@@ -480,25 +497,48 @@ cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t* vps) {
-  *mtiles = (27 * cin + kM - 1) / kM;
-  int ns = (4 * sms + *mtiles - 1) / *mtiles;
-  const size_t per = (nvox + ns - 1) / ns;
-  *vps = ((per + kWgK - 1) / kWgK) * kWgK;
-  if (*vps == 0) *vps = kWgK;
-  *nsplit = static_cast<int>((nvox + *vps - 1) / *vps);
-  if (*nsplit < 1) *nsplit = 1;
+void wgrad_plan(int d, int h, int w, int cin, int sms, int* nsplit, int* tiles_per_split) {
+  // one CTA per SM over all input-channel chunks (shared memory and TMEM
+  // allow one per SM); the tiles split evenly
+  const long tiles = static_cast<long>((w + kConvTW - 1) / kConvTW) * ((h + kConvTH - 1) / kConvTH) * d;
+  const int chunks = cin / 16;
+  long ns = sms / chunks;          // at most one wave
+  if (ns > tiles) ns = tiles;
+  if (ns < 1) ns = 1;
+  *tiles_per_split = static_cast<int>((tiles + ns - 1) / ns);
+  *nsplit = static_cast<int>((tiles + *tiles_per_split - 1) / *tiles_per_split);
 }
 
 cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s) {
-  dim3 grid(a.mtiles, a.nsplit);
-  const size_t smem = wgrad_smem_bytes(a.cout);
-  cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  if (a.cin % 16 != 0 || a.cin / 8 > kConvMaxGroups || a.cout % 8 != 0 || a.cout > 64)
+    return cudaErrorInvalidValue;
+  WgradMaps maps;
+  const cuuint32_t xbox[4] = {8, kConvHX, kConvTH + 2, 3};
+  const cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(a.w), static_cast<cuuint64_t>(a.h),
+                              static_cast<cuuint64_t>(a.d)};
+  const cuuint64_t xrow = static_cast<cuuint64_t>(a.cin) * 2;
+  const cuuint64_t xstr[3] = {xrow, xrow * a.w, xrow * a.w * a.h};
+  for (int g = 0; g < a.cin / 8; ++g) {
+    cudaError_t e = encode_tmap(&maps.x[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, a.x + g * 8, dims,
+                                xstr, xbox);
+    if (e != cudaSuccess) return e;
+  }
+  const cuuint32_t gbox[4] = {8, kConvTW, kConvTH, 1};
+  const cuuint64_t grow = static_cast<cuuint64_t>(a.cout) * 2;
+  const cuuint64_t gstr[3] = {grow, grow * a.w, grow * a.w * a.h};
+  for (int g = 0; g < a.cout / 8; ++g) {
+    cudaError_t e = encode_tmap(&maps.gy[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, a.gy + g * 8, dims,
+                                gstr, gbox);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kWgSmem);
   if (e != cudaSuccess) return e;
-  k_conv_wgrad<<<grid, kThreads, smem, s>>>(a);
+  dim3 grid(a.nsplit, a.cin / 16);
+  k_conv_wgrad_tile<<<grid, kThreads, kWgSmem, s>>>(a, maps);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_wgrad_reduce<<<128, 256, 0, s>>>(a.partial, a.nsplit, a.mtiles * kM, a.cin, a.cout, gw);
+  const int total = a.cout * 27 * a.cin;
+  k_wgrad_reduce<<<128, 256, 0, s>>>(a.partial, a.nsplit, total, gw);
   return cudaGetLastError();
 }
 

@@ -428,10 +428,9 @@ rihv_status rihv_nn_conv3d_dgrad(const uint16_t* gy, const uint16_t* w, void* gx
 
 size_t rihv_nn_conv3d_wgrad_workspace(int d, int h, int wd, int c_in, int c_out) {
   if (d < 1 || h < 1 || wd < 1 || c_in < 16 || c_out < 16) return 0;
-  int mt = 0, ns = 0;
-  size_t vps = 0;
-  wgrad_plan(static_cast<size_t>(d) * h * wd, c_in, device_sms(), &mt, &ns, &vps);
-  return static_cast<size_t>(ns) * mt * 128 * c_out * sizeof(float);
+  int ns = 0, tps = 0;
+  wgrad_plan(d, h, wd, c_in, device_sms(), &ns, &tps);
+  return static_cast<size_t>(ns) * c_out * 27 * c_in * sizeof(float);
 }
 
 rihv_status rihv_nn_conv3d_wgrad(const uint16_t* x, const uint16_t* gy, float* gw, int d, int h,
@@ -453,8 +452,7 @@ rihv_status rihv_nn_conv3d_wgrad(const uint16_t* x, const uint16_t* gy, float* g
   a.cin = c_in;
   a.cout = c_out;
   a.err = err_flag;
-  wgrad_plan(static_cast<size_t>(d) * h * wd, c_in, device_sms(), &a.mtiles, &a.nsplit,
-             &a.vox_per_split);
+  wgrad_plan(d, h, wd, c_in, device_sms(), &a.nsplit, &a.tiles_per_split);
   return launch_wgrad(a, gw, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RIHV_OK
                                                                               : RIHV_ERR_CUDA;
 }

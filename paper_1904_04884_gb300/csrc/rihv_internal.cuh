@@ -293,10 +293,10 @@ struct ConvArgs {
 struct WgradArgs {
   const __nv_bfloat16* x;   // [voxels][cin]
   const __nv_bfloat16* gy;  // [voxels][cout]
-  float* partial;           // [nsplit][mtiles*128][cout]
+  float* partial;           // [nsplit][cout][27][cin]
   int d, h, w, cin, cout;
-  int mtiles, nsplit;
-  size_t vox_per_split;
+  int nsplit;               // CTAs per 16-channel input chunk (grid.x)
+  int tiles_per_split;      // 128 x 2 voxel tiles of one CTA
   int* err;
 };
 // Halo-tile geometry of the forward / input-gradient convolution.
@@ -317,7 +317,8 @@ cudaError_t launch_conv(bool dgrad, const ConvArgs& a, cudaStream_t s);
 // fill out of bounds); rank <= 5, strides in bytes for dims 1..rank-1.
 cudaError_t encode_tmap(CUtensorMap* tm, CUtensorMapDataType type, int rank, const void* base,
                         const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box);
-void wgrad_plan(size_t nvox, int cin, int sms, int* mtiles, int* nsplit, size_t* vps);
+// CTAs per input-channel chunk and tiles per CTA of the weight gradient.
+void wgrad_plan(int d, int h, int w, int cin, int sms, int* nsplit, int* tiles_per_split);
 cudaError_t launch_wgrad(const WgradArgs& a, float* gw, cudaStream_t s);
 size_t conv_smem_bytes(int ck, int n);
 
