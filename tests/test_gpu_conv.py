@@ -112,3 +112,17 @@ def test_pool_upsample_concat_relu_and_bias_grad():
     work = torch.empty(256 * c, dtype=torch.float64, device=DEV)
     nn.bias_grad(xd, gb, nvox, c, work)
     np.testing.assert_allclose(gb.cpu().numpy(), x.double().numpy().sum(axis=0), rtol=1e-6, atol=1e-5)
+
+
+@pytest.mark.parametrize("c", [16, 32, 64, 48])
+def test_bias_grad_large(c):
+    """gb[c] = sum over voxels of gy[v][c] on a ragged voxel count (the
+    vectorised reduction over 8-channel words), against an FP64 sum."""
+    nvox = 300_007
+    gy = _bf16((nvox, c), 9 + c)
+    gb = torch.empty(c, dtype=torch.float32, device=DEV)
+    work = torch.empty(256 * c, dtype=torch.float64, device=DEV)
+    nn.bias_grad(gy.to(DEV), gb, nvox, c, work)
+    torch.cuda.synchronize()
+    ref = gy.double().numpy().sum(axis=0)
+    np.testing.assert_allclose(gb.cpu().numpy(), ref, rtol=1e-6, atol=1e-4)
