@@ -394,19 +394,25 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad_tile(const __grid_const
       loaded_wait = i;
       tc_fence_after();
       const uint32_t sg = base + st * kWgStage;
-      const uint32_t sh = sg + kWgGyBytes;
-      for (int t = 0; t < 27; ++t) {
-        int dz, dy, dx;
-        tap_offset(t, dz, dy, dx);
-        for (int mt = 0; mt < kConvTH; ++mt) {
-          for (int k = 0; k < kConvTW / 16; ++k) {
-            const uint64_t ad = smem_desc(sg + mt * (kConvTW * 16) + k * 256, 128, kWgGyBytes / 8);
-            const uint32_t hoff = (((dz + 1) * (kConvTH + 2) + mt + dy + 1) * kConvHX + 16 * k + dx + 1) * 16;
-            const uint64_t bd = smem_desc(sh + hoff, 128, kConvHaloKu);
-            umma_bf16(tmem + t * 16, ad, bd, idesc, (i > 0 || mt > 0 || k > 0) ? 1u : 0u);
+      // descriptors differ only in the start address (bits 0-13, in 16-byte
+      // units, no carry: shared addresses stay below 256 KB), so each MMA
+      // adds an offset to one of two base descriptors
+      const uint64_t ad0 = smem_desc(sg, 128, kWgGyBytes / 8);
+      const uint64_t bd0 = smem_desc(sg + kWgGyBytes, 128, kConvHaloKu);
+      const uint32_t acc0 = i > 0 ? 1u : 0u;
+      for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy)
+          for (int dx = 0; dx < 3; ++dx) {
+            const uint32_t dcol = tmem + (dz * 9 + dy * 3 + dx) * 16;
+#pragma unroll
+            for (int mt = 0; mt < kConvTH; ++mt) {
+              const uint64_t brow = bd0 + ((dz * (kConvTH + 2) + mt + dy) * kConvHX + dx);
+              const uint64_t arow = ad0 + mt * (kConvTW * 16 / 16);
+#pragma unroll
+              for (int k = 0; k < kConvTW / 16; ++k)
+                umma_bf16(dcol, arow + k * 16, brow + k * 16, idesc, (acc0 | mt | k) ? 1u : 0u);
+            }
           }
-        }
-      }
       umma_commit(saddr(&bars[2 + st]));
       committed = i;
       if (i + 1 < n) {
