@@ -744,6 +744,16 @@ rihv_status solve_fasta(rihv_ctx* h, bool warm, float l1, float ltv, int iters, 
                         int* done_out) {
   if (!h->fasta_g[0]) return fail(h, RIHV_ERR_INVALID_ARG, "FASTA scratch not allocated");
   const size_t vb = h->nvox * sizeof(float2);
+  // The accepted candidate swaps buffers with x. Graphs captured earlier hold
+  // the address of h->x, so it is handed back on every return (with the
+  // result copied into it on success).
+  struct XHome {
+    rihv_ctx* h;
+    float2* home;
+    ~XHome() {
+      if (h->x != home) std::swap(h->x, h->fasta_x);
+    }
+  } x_home{h, h->x};
   const float gscale = static_cast<float>(2.0 / static_cast<double>(h->nxy));
   CKS(fft2_plane(h, h->holo, true, h->bhat));
   if (!warm) CK(cudaMemsetAsync(h->x, 0, vb, h->stream));
@@ -819,6 +829,8 @@ rihv_status solve_fasta(rihv_ctx* h, bool warm, float l1, float ltv, int iters, 
       }
     }
   }
+  if (h->x != x_home.home)
+    CK(cudaMemcpyAsync(x_home.home, h->x, vb, cudaMemcpyDeviceToDevice, h->stream));
   *check_out = check;
   *done_out = done;
   return RIHV_OK;
