@@ -104,3 +104,29 @@ def test_fasta_stop_test_and_batch_refusal():
     assert done == first < 40 and tr2[done // 5 - 1] <= tr[-1] * 1.1
     with pytest.raises(RihvError):
         Batch([h]).solve([b], w.lam_l1, w.lam_tv, 10, [x])
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_fasta_between_batched_solves(warm):
+    """A FASTA solve ends with x in whichever of its two buffers took the last
+    accepted step; a batched graph captured before it must still find its
+    input and its result where it left them. The batch's results before and
+    after a FASTA solve of an odd number of iterations on the same handle
+    agree bit for bit."""
+    w, op, b = _tiny()
+    h = handle(op, n_inner=w.n_inner, check_every=0)
+    bt = Batch([h])
+    x0 = [torch.from_numpy(0.1 * synth.random_complex(synth.Stream(77), op.shape)
+                           .astype(np.complex64)).cuda()] if warm else None
+    x1 = torch.empty(op.shape, dtype=torch.complex64, device="cuda:0")
+    bt.solve([b], w.lam_l1, w.lam_tv, 10, [x1], x0s=x0)
+    h.set_options(n_inner=w.n_inner, check_every=0, solver=1)
+    xf = torch.empty_like(x1)
+    h.solve(b, w.lam_l1, w.lam_tv, 7, xf)
+    same_parts = [(d["first"], d["nvox"]) for d in h.detect(xf)]
+    assert [(d["first"], d["nvox"]) for d in h.detect(None)] == same_parts
+    h.set_options(n_inner=w.n_inner, check_every=0)
+    x2 = torch.empty_like(x1)
+    bt.solve([b], w.lam_l1, w.lam_tv, 10, [x2], x0s=x0)
+    assert torch.equal(x1, x2)
+    assert not torch.equal(x1, xf)
