@@ -101,8 +101,8 @@ typedef struct {
                         product's summation order in the fused finalize.    */
   int fft_rows_per_cta; /* rows transformed per CTA in the row passes of the
                         register FFT engine (power-of-two nx): 0 (default)
-                        takes 4 or the autotuner's choice; otherwise 2, 4 or
-                        8, dividing ny. Same arithmetic for every value.    */
+                        takes 4 or the autotuner's choice; otherwise 1, 2, 4
+                        or 8, dividing ny. Same arithmetic for every value. */
   int tv_fgp;        /* 1: the TV prox runs the accelerated dual iteration
                         (Beck-Teboulle's fast gradient projection: each step
                         taken at r_k = p_{k-1} + ((t_{k-1} - 1)/t_k)(p_{k-1} -
@@ -252,7 +252,7 @@ rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done);
 /* Autotuner (not in the paper). Times, on the handle's own scratch, the TV
  * kernel's z-chunk length (8..256 planes per CTA) and steps per launch (1 or
  * 2, i.e. halo depth), the number of planes each column-pass CTA sums
- * (z-group size), and the row-pass FFT tile (2, 4 or 8 rows per CTA, for
+ * (z-group size), and the row-pass FFT tile (1, 2, 4 or 8 rows per CTA, for
  * power-of-two nx), then applies the fastest to the handle. With a non-NULL
  * cache_path the result is looked up first (key: nx ny nz tv_dims) and
  * appended after a search, one line per shape. chosen_or_null (int[4])

@@ -398,10 +398,13 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_cols(const __grid_constant__
 // product of the earlier radices); for the last pass that is b + m N/R, the
 // same per-thread set again, so the result stays in registers in natural
 // order. Passes in between exchange through shared memory (one barrier per
-// exchange, two buffers alternating), indexed l ^ ((l >> 3) & 15), which
-// makes every half-warp's 8-byte accesses of all passes conflict-free with
-// four interleaved teams (thread = 4 i + team, rows 4 elements apart). The
-// first pass reads from global memory and the last writes to it directly.
+// exchange, two buffers alternating), indexed l ^ ((l >> 3) & 15), with NT
+// interleaved teams (thread = NT i + team) whose rows are N + 16/NT elements
+// apart: every half-warp's 8-byte accesses of all passes are then
+// conflict-free for NT = 1, 2, 4 and 8. Twiddles come from a pass-major table
+// (pass s: w^(j k) at [(j - 1) P + k]), where lanes on consecutive k read
+// consecutive words. The first pass reads from global memory and the last
+// writes to it directly.
 // ---------------------------------------------------------------------------
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 
@@ -409,9 +412,12 @@ template <int N, int NT = 4>
 struct RShape {
   static constexpr int TT = N / 8;                                  // threads per transform
   static constexpr int NP = ilog2c(N) / 3 + (ilog2c(N) % 3 ? 1 : 0);  // passes
-  static constexpr int LDX = N + 4;                                 // exchange row stride
+  static constexpr int LDX = N + 16 / NT;                           // exchange row stride
   static constexpr int kTeams = NT;                                 // transforms per CTA
   static constexpr int kThreads = kTeams * TT;
+  // one-row tiles: small CTAs, several per SM, each waiting only on its own
+  // barriers; registers capped for 24 resident warps (about 85 per thread)
+  static constexpr int kMinBlocks = (NT == 1 && kThreads < 768) ? 768 / kThreads : 1;
   __host__ __device__ static constexpr int radix(int s) {
     return s < ilog2c(N) / 3 ? 8 : (1 << (ilog2c(N) % 3));
   }
@@ -421,6 +427,39 @@ struct RShape {
 };
 
 __device__ __forceinline__ int xswz(int l) { return l ^ ((l >> 3) & 15); }
+
+// Offset of pass s's twiddles in the pass-major table (passes with P = 1 have
+// none); the whole table has fewer than N entries.
+template <int N>
+__host__ __device__ constexpr int rtw_offset(int s) {
+  int off = 0, p = 1;
+  for (int t = 0; t < s; ++t) {
+    const int r = RShape<N>::radix(t);
+    if (p > 1) off += (r - 1) * p;
+    p *= r;
+  }
+  return off;
+}
+
+// Builds the pass-major table in shared memory from the length-N table
+// exp(-2 pi i m / N): entry (j - 1) P + k of pass s is w^(j k N / (P R)).
+template <int N>
+__device__ __forceinline__ void stage_rtw(float2* dst, const float2* __restrict__ src) {
+  static_assert(rtw_offset<N>(RShape<N>::NP) <= N, "twiddle table exceeds its shared buffer");
+  int off = 0, p = 1;
+#pragma unroll
+  for (int s = 0; s < RShape<N>::NP; ++s) {
+    const int r = RShape<N>::radix(s);
+    if (p > 1) {
+      for (int idx = threadIdx.x; idx < (r - 1) * p; idx += blockDim.x) {
+        const int j = idx / p + 1, k = idx - (j - 1) * p;
+        dst[off + idx] = src[j * k * (N / (p * r))];
+      }
+      off += (r - 1) * p;
+    }
+    p *= r;
+  }
+}
 
 template <int N, bool INV, int S, int P>
 __device__ __forceinline__ void rfft_passes(float2 (&v)[8], int i, float2* xa, float2* xb,
@@ -440,7 +479,7 @@ __device__ __forceinline__ void rfft_passes(float2 (&v)[8], int i, float2* xa, f
       if constexpr (P > 1) {
 #pragma unroll
         for (int j = 1; j < R; ++j) {
-          const float2 w = tw[j * k * (N / (P * R))];
+          const float2 w = tw[rtw_offset<N>(S) + (j - 1) * P + k];
           u[j] = INV ? cmulc(u[j], w) : cmul(u[j], w);
         }
       }
@@ -478,12 +517,12 @@ __device__ __forceinline__ void rfft(float2 (&v)[8], int i, float2*& xa, float2*
 // Row pass, register engine: NT rows of one plane per item (team = row; 4 by
 // default, 2 or 8 when the autotuner finds them faster for a grid).
 template <bool INV, int IN, int OUT, int EPI, int N, int NT_ = 4>
-__global__ void __launch_bounds__(RShape<N, NT_>::kThreads) k_rows_reg(const __grid_constant__ RowArgs a) {
+__global__ void __launch_bounds__(RShape<N, NT_>::kThreads, RShape<N, NT_>::kMinBlocks) k_rows_reg(const __grid_constant__ RowArgs a) {
   using Sh = RShape<N, NT_>;
   constexpr int TT = Sh::TT, W = kStrip, NT = Sh::kTeams;
   extern __shared__ float2 smem[];
   float2* tw = smem;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = a.tw[m];
+  stage_rtw<N>(tw, a.tw);
   const int i = threadIdx.x / NT, team = threadIdx.x % NT;
   float2* xa = smem + N + team * Sh::LDX;
   float2* xb = xa + NT * Sh::LDX;
@@ -566,7 +605,7 @@ __global__ void __launch_bounds__(RShape<N>::kThreads) k_cols_reg(const __grid_c
   static_assert(NT == W, "one team per strip column");
   extern __shared__ float2 smem[];
   float2* tw = smem;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) tw[m] = a.tw[m];
+  stage_rtw<N>(tw, a.tw);
   const int i = threadIdx.x / NT, w = threadIdx.x % NT;
   float2* xa = smem + N + w * Sh::LDX;
   float2* xb = xa + NT * Sh::LDX;
@@ -806,6 +845,7 @@ cudaError_t launch_rows_reg_t(const RowArgs& a, cudaStream_t s) {
 template <bool INV, int IN, int OUT, int EPI, int N>
 cudaError_t launch_rows_reg(const RowArgs& a, cudaStream_t s) {
   switch (a.teams) {
+    case 1: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 1>(a, s);
     case 2: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 2>(a, s);
     case 8: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 8>(a, s);
     default: return launch_rows_reg_t<INV, IN, OUT, EPI, N, 4>(a, s);
@@ -874,7 +914,8 @@ cudaError_t launch_cols_t(const ColArgs& a, int groups, cudaStream_t s) {
 bool reg_length(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
 
 size_t rows_smem_bytes(int nx, int teams) {
-  if (reg_length(nx)) return sizeof(float2) * (nx + 2 * static_cast<size_t>(teams) * (nx + 4));
+  if (reg_length(nx))
+    return sizeof(float2) * (nx + 2 * static_cast<size_t>(teams) * (nx + 16 / teams));
   return sizeof(float2) * (2 * static_cast<size_t>(nx) * (kRowsPerCta + 1) + nx);
 }
 

@@ -1044,8 +1044,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       (o->fuse_finalize != 0 && o->fuse_finalize != 1) ||
       (o->skip_empty_planes != 0 && o->skip_empty_planes != 1) ||
       (o->tv_zchunk != 0 && (o->tv_zchunk < std::min(8, h->nz) || o->tv_zchunk > kTvMaxChunk)) ||
-      (o->fft_rows_per_cta != 0 && o->fft_rows_per_cta != 2 && o->fft_rows_per_cta != 4 &&
-       o->fft_rows_per_cta != 8) ||
+      (o->fft_rows_per_cta != 0 && o->fft_rows_per_cta != 1 && o->fft_rows_per_cta != 2 &&
+       o->fft_rows_per_cta != 4 && o->fft_rows_per_cta != 8) ||
       (o->fft_rows_per_cta != 0 && h->ny % o->fft_rows_per_cta != 0) ||
       (o->tv_fgp != 0 && o->tv_fgp != 1) || (o->solver != 0 && o->solver != 1))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
@@ -1812,8 +1812,8 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
         zpg = c;
       }
     }
-    // row-pass tile: transforms per CTA of the register engine (2, 4 or 8
-    // rows), with the chosen column z-groups
+    // row-pass tile: transforms per CTA of the register engine (1, 2, 4 or
+    // 8 rows), with the chosen column z-groups
     teams = 4;
     if (reg_length(h->nx) && st == RIHV_OK) {
       h->zpg = zpg;

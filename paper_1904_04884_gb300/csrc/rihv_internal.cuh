@@ -108,7 +108,7 @@ struct RowArgs {
   const int* occ;      // forward rows (complex input): [nz + 1] plane occupancy; when
                        // occ[nz] != 0, planes z with occ[z] == 0 are all zero and
                        // skipped (nothing written); null: every plane
-  int teams;           // register engine: rows (transforms) per CTA, 2, 4 or 8 (0: 4)
+  int teams;           // register engine: rows (transforms) per CTA, 1, 2, 4 or 8 (0: 4)
 };
 
 enum ColMode { COL_FWD_ZSUM = 0, COL_ADJ_GEN = 1, COL_PLAIN_FWD = 2, COL_PLAIN_INV = 3 };
@@ -131,7 +131,7 @@ cudaError_t launch_rows(int dir_inverse, int in, int out, int epi, const RowArgs
                         cudaStream_t s);
 cudaError_t launch_cols(int mode, const ColArgs& a, int groups, cudaStream_t s);
 size_t rows_smem_bytes(int nx, int teams = 4);
-constexpr int kRowTeams[3] = {2, 4, 8};   // row-pass tile shapes the autotuner tries
+constexpr int kRowTeams[4] = {1, 2, 4, 8};   // row-pass tile shapes the autotuner tries
 size_t cols_smem_bytes(int mode, int ny);
 bool reg_length(int n);   // lengths served by the register FFT engine
 // Resident CTAs per SM of the forward column pass for this ny (sizes the z-groups).

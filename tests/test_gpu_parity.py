@@ -69,10 +69,10 @@ def test_adjoint_parity(nx, ny, nz):
     assert rel_l2(out.cpu().numpy(), O.adjoint(r, op)) <= OP_TOL
 
 
-@pytest.mark.parametrize("rows", [2, 4, 8])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
 @pytest.mark.parametrize("nx,ny,nz", [(128, 64, 5), (1024, 16, 2), (64, 256, 9)])
 def test_row_tile_shapes_match_oracle(nx, ny, nz, rows):
-    """Every row-pass tile of the register FFT engine (2, 4 or 8 rows per CTA)
+    """Every row-pass tile of the register FFT engine (1, 2, 4 or 8 rows per CTA)
     gives the forward and the adjoint to the operator tolerance."""
     op = optics(nx, ny, nz)
     h = handle(op)
