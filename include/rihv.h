@@ -101,8 +101,9 @@ typedef struct {
                         product's summation order in the fused finalize.    */
   int fft_rows_per_cta; /* rows transformed per CTA in the row passes of the
                         register FFT engine (power-of-two nx): 0 (default)
-                        takes 4 or the autotuner's choice; otherwise 1, 2, 4
-                        or 8, dividing ny. Same arithmetic for every value. */
+                        takes the autotuner's choice, else 2 for nx >= 512
+                        and 4 below; otherwise 1, 2, 4 or 8, dividing ny.
+                        Same arithmetic for every value.                    */
   int tv_fgp;        /* 1: the TV prox runs the accelerated dual iteration
                         (Beck-Teboulle's fast gradient projection: each step
                         taken at r_k = p_{k-1} + ((t_{k-1} - 1)/t_k)(p_{k-1} -

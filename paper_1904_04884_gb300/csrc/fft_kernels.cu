@@ -415,9 +415,10 @@ struct RShape {
   static constexpr int LDX = N + 16 / NT;                           // exchange row stride
   static constexpr int kTeams = NT;                                 // transforms per CTA
   static constexpr int kThreads = kTeams * TT;
-  // one-row tiles: small CTAs, several per SM, each waiting only on its own
-  // barriers; registers capped for 24 resident warps (about 85 per thread)
-  static constexpr int kMinBlocks = (NT == 1 && kThreads < 768) ? 768 / kThreads : 1;
+  // row passes: registers capped for at least 24 resident warps (about 85 per
+  // thread) when the CTA is small enough for several per SM, each waiting
+  // only on its own barriers
+  static constexpr int kMinBlocks = kThreads < 768 ? 768 / kThreads : 1;
   __host__ __device__ static constexpr int radix(int s) {
     return s < ilog2c(N) / 3 ? 8 : (1 << (ilog2c(N) % 3));
   }

@@ -107,7 +107,7 @@ struct rihv_ctx {
   int groups = 1, zpg = 1;
   int sms = 152;
   int tv_zchunk = 0;                 // planes per TV z-chunk; 0: tv_default_zchunk
-  int row_teams = 0;                 // rows per CTA of the register row pass; 0: 4
+  int row_teams = 0;                 // rows per CTA of the register row pass; 0: the default
   bool batch_chunks = false;         // being captured into a batched graph (see tv_steps)
   double* fin_partials = nullptr;    // one per CTA of a fused-finalize TV launch
   int fin_ctas = 0;                  // capacity of fin_partials
@@ -286,6 +286,10 @@ struct StageScope {
 };
 
 // ---- stage drivers ----------------------------------------------------------
+// Rows per CTA of the register row pass when neither the options nor the
+// autotuner chose: 2 from length 512 up (three CTAs per SM), else 4.
+int default_row_teams(int nx, int ny) { return (nx >= 512 && ny % 2 == 0) ? 2 : 4; }
+
 RowArgs row_args(rihv_ctx* h, const void* src, float2* dst, int nz) {
   RowArgs a{};
   a.src = src;
@@ -296,7 +300,9 @@ RowArgs row_args(rihv_ctx* h, const void* src, float2* dst, int nz) {
   a.scale = 1.f;
   a.plan = h->plan_x;
   a.tw = h->tw_x;
-  a.teams = h->opt.fft_rows_per_cta > 0 ? h->opt.fft_rows_per_cta : h->row_teams;
+  a.teams = h->opt.fft_rows_per_cta > 0 ? h->opt.fft_rows_per_cta
+            : h->row_teams > 0           ? h->row_teams
+                                         : default_row_teams(h->nx, h->ny);
   return a;
 }
 
@@ -1814,7 +1820,8 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
     }
     // row-pass tile: transforms per CTA of the register engine (1, 2, 4 or
     // 8 rows), with the chosen column z-groups
-    teams = 4;
+    const int teams0 = default_row_teams(h->nx, h->ny);
+    teams = teams0;
     if (reg_length(h->nx) && st == RIHV_OK) {
       h->zpg = zpg;
       h->groups = (h->nz + zpg - 1) / zpg;
@@ -1828,7 +1835,8 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {
           return adjoint_planes(h, h->spec, h->y, h->v, gs, true);
         }, 3, &st);
         if (st != RIHV_OK) break;
-        if (ms < best * 0.99 || (t == 4 && ms < best * 1.01)) {   // 4 unless clearly slower
+        // the default unless clearly slower
+        if (ms < best * 0.99 || (t == teams0 && ms < best * 1.01)) {
           best = ms;
           teams = t;
         }
