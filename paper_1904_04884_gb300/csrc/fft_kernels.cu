@@ -429,6 +429,32 @@ struct RShape {
 
 __device__ __forceinline__ int xswz(int l) { return l ^ ((l >> 3) & 15); }
 
+// xswz((b - k) R + k + m P), k = b mod P: the exchange position of output m of
+// butterfly b. From P = 64 up, (b - k) R, m P and k occupy disjoint bits and
+// the swizzle only changes k's low four bits, so the position is a
+// per-thread base plus a compile-time offset m P (for P = 64, bit 3 of the
+// base also follows m's parity). Identical to xswz for every position.
+template <int R, int P>
+__device__ __forceinline__ int xpos(int b, int k, int m) {
+  if constexpr (P >= 128)
+    return (b - k) * R + (k ^ ((k >> 3) & 15)) + m * P;
+  else if constexpr (P == 64)
+    return (b - k) * R + ((k ^ (k >> 3)) ^ ((m & 1) << 3)) + m * P;
+  else
+    return xswz((b - k) * R + k + m * P);
+}
+
+// xswz(i + TT e) for i < TT: with TT a multiple of 16 the swizzle term is
+// ((i >> 3) + (TT / 8) e) mod 16 and leaves TT e untouched, so the position is
+// a per-thread base (at most four distinct ones) plus the offset TT e.
+template <int TT>
+__device__ __forceinline__ int xrd(int i, int e) {
+  if constexpr (TT >= 16)
+    return (i ^ (((i >> 3) + (TT / 8) * e) & 15)) + TT * e;
+  else
+    return xswz(i + TT * e);
+}
+
 // Offset of pass s's twiddles in the pass-major table (passes with P = 1 have
 // none); the whole table has fewer than N entries.
 template <int N>
@@ -490,13 +516,13 @@ __device__ __forceinline__ void rfft_passes(float2 (&v)[8], int i, float2* xa, f
         if constexpr (LAST)
           v[q + m * (8 / R)] = u[m];
         else
-          xs[xswz((b - k) * R + k + m * P)] = u[m];
+          xs[xpos<R, P>(b, k, m)] = u[m];
       }
     }
     if constexpr (!LAST) {
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = xs[xswz(i + TT * e)];
+      for (int e = 0; e < 8; ++e) v[e] = xs[xrd<TT>(i, e)];
     }
     rfft_passes<N, INV, S + 1, P * R>(v, i, xa, xb, tw);
   }

@@ -129,3 +129,32 @@ def test_a_pitch_of_n_plus_4_conflicts_for_two_and_eight_teams():
         return actual / ideal
     assert ratio_with_pitch(1024, 2, 4) > 1.0 and ratio_with_pitch(1024, 8, 4) > 1.0
     assert ratio_with_pitch(1024, 2, 8) == 1.0 and ratio_with_pitch(1024, 8, 2) == 1.0
+
+
+def test_closed_form_positions_equal_the_swizzle():
+    """The kernels compute exchange positions as a per-thread base plus a
+    compile-time offset (xpos for writes from P = 64 up, xrd for reads with
+    N/8 >= 16); both are identities of the swizzled index for every length,
+    pass, butterfly and element."""
+    def xpos(r, p, b, k, m):
+        if p >= 128:
+            return (b - k) * r + (k ^ ((k >> 3) & 15)) + m * p
+        if p == 64:
+            return (b - k) * r + ((k ^ (k >> 3)) ^ ((m & 1) << 3)) + m * p
+        return xswz((b - k) * r + k + m * p)
+
+    def xrd(tt, i, e):
+        return (i ^ (((i >> 3) + (tt // 8) * e) & 15)) + tt * e if tt >= 16 else xswz(i + tt * e)
+
+    for n in LENGTHS:
+        tt, p = n // 8, 1
+        for r in radices(n):
+            for i in range(tt):
+                for q in range(8 // r):
+                    b = i + q * tt
+                    k = b & (p - 1)
+                    for m in range(r):
+                        assert xpos(r, p, b, k, m) == xswz((b - k) * r + k + m * p)
+                for e in range(8):
+                    assert xrd(tt, i, e) == xswz(i + tt * e)
+            p *= r
