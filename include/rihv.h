@@ -178,7 +178,10 @@ rihv_status rihv_prox_fused_lasso(rihv_handle h, const void* v, float t_l1, floa
  * If *iters_done is non-NULL it receives the iterations actually run (fewer
  * than iters only when the f_star stop test fired). The call returns after
  * the stream has finished the solve; a non-finite objective or norm returns
- * RIHV_ERR_NONFINITE. */
+ * RIHV_ERR_NONFINITE. Host buffers are read by the CPU, one byte per page,
+ * just before the device copies them (x_out once the iterations have run):
+ * without it the first device-to-host copy into pinned pages the CPU had
+ * not touched for seconds ran several times slower. */
 rihv_status rihv_solve(rihv_handle h, const float* hologram, float lambda_l1, float lambda_tv,
                        int iters, const void* x0_or_null, void* x_out,
                        double* objective_trace_or_null, int* iters_done);
