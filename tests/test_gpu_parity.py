@@ -389,3 +389,26 @@ def test_short_solve_parity_on_ragged_grids(nx, ny, nz, dims):
     ref, tr_ref = O.fista(b.astype(np.float64), op, 0.01, 0.005, 5, 6, dims, check_every=1)
     assert rel_l2(x.cpu().numpy(), ref) <= 1e-4
     np.testing.assert_allclose(tr, [f for _, f in tr_ref], rtol=1e-5)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(128, 64, 9), (512, 32, 3), (1024, 16, 2)])
+def test_solve_with_every_row_tile(nx, ny, nz):
+    """Five FISTA iterations with 1, 2, 4 and 8 rows per row-pass CTA (the
+    inverse row pass then runs its gradient-step epilogue in each tile
+    shape): the same iterate bit for bit, and the oracle's to 1e-4."""
+    op = optics(nx, ny, nz)
+    a = np.zeros(op.shape)
+    a[nz // 2, ny // 3:ny // 3 + 3, nx // 4:nx // 4 + 3] = 1.0
+    b = synth.intensity_hologram(O.forward(a, op), 0.01, synth.Stream(nx + 3 * nz).normal(nx * ny))
+    outs = []
+    for rows in (1, 2, 4, 8):
+        h = handle(op)
+        h.set_options(n_inner=4, check_every=0, fft_rows_per_cta=rows)
+        x = torch.empty(op.shape, dtype=torch.complex64, device=dev())
+        h.solve(b, 0.01, 0.005, 5, x)
+        outs.append(x.cpu())
+        h.close()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    ref, _ = O.fista(b.astype(np.float64), op, 0.01, 0.005, 5, 4, 3)
+    assert rel_l2(outs[0].numpy(), ref) <= 1e-4
