@@ -59,7 +59,7 @@ typedef enum {
 /* Solver options. Defaults (rihv_default_options): tv_dims 3, restart 1,
  * accelerate 1, n_inner 20, check_every 10, tol 0, f_star 0,
  * tv_steps_per_launch 2, fuse_finalize 1, skip_empty_planes 0, tv_zchunk 0,
- * fft_rows_per_cta 0, tv_fgp 0, solver 0. */
+ * fft_rows_per_cta 0, tv_fgp 0, solver 0, tv_split 1. */
 typedef struct {
   int tv_dims;       /* 3: 3D isotropic TV; 2: plane-wise 2D TV (Section 2,
                         TV prox paragraph restricts TV to planes)            */
@@ -118,6 +118,13 @@ typedef struct {
                         test, at most 20 times; first step 1/L); its host
                         loop synchronises twice per iteration, and the first
                         use allocates two gradient volumes and a candidate.  */
+  int tv_split;      /* 1 (default): two-step TV launches whose equal z-chunks
+                        would leave the last wave of CTAs partly idle cut the
+                        last tiles into 2-4 shorter z-chunks, launched after
+                        the rest (chosen by a makespan model of the launch,
+                        taken when it saves at least 2 %); 0: equal z-chunks
+                        for every tile. Results do not depend on it, except
+                        the FISTA restart product's summation order.        */
 } rihv_options;
 
 /* One detected particle (Section 2, segmentation paragraph). */
@@ -264,6 +271,13 @@ rihv_status rihv_batch_iterations(rihv_batch b, int* iters_done);
  * row-pass CTA}. Synchronises; the scratch contents (x, y, v) are
  * overwritten. An option tv_zchunk > 0 overrides the tuned z-chunk. */
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_null);
+
+/* The z-chunking a two-step TV launch of a solve on this handle uses (not in
+ * the paper): final = 0 for the launches that read the dual (and the first
+ * of a prox), 1 for the fused-finalize launch. out3 receives {planes per
+ * z-chunk, split_tile, planes per z-chunk from split_tile on (0: no split)}
+ * (option tv_split). Host-only; no device work. */
+rihv_status rihv_tv_schedule(rihv_handle h, int final, int* out3);
 
 /* Steps of the last rihv_solve run with the FASTA-style solver (option
  * solver = 1; not in the paper beyond its naming FASTA): the accepted step

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -134,6 +135,11 @@ struct rihv_ctx {
   bool batch_chunks = false;         // being captured into a batched graph (see tv_steps)
   double* fin_partials = nullptr;    // one per CTA of a fused-finalize TV launch
   int fin_ctas = 0;                  // capacity of fin_partials
+  // z-chunk splits of the two-step TV launches, by launch tile ([0] reading
+  // p or first, [1] fused final), for the z-chunk they were computed for
+  struct TvSplitCache {
+    int zchunk = -1, split_tile = 0, zchunk2 = 0;
+  } tv_split[2];
   double tau = 0;
   FftPlan plan_x{}, plan_y{};
   std::string err;
@@ -406,6 +412,70 @@ int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
   return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
 }
 
+// Split of a two-step TV launch (TvArgs::split_tile, zchunk2). With one CTA
+// per SM, equal z-chunks leave the last wave partly idle (at 1024x1024x256,
+// 1,152 CTAs fill 7.6 waves). Model: a CTA of c planes takes c + halo plane
+// ticks and CTAs start in launch order on the first free SM. The last r
+// tiles are cut into m = 2, 3 or 4 z-chunks (of at least 8 planes) and
+// launched after the rest; the split with the shortest modelled makespan is
+// taken if it saves at least 2 % over equal chunks.
+void tv_choose_split(int ntiles, int nz, int zc, int halo, int sms, int* split_tile,
+                     int* zchunk2) {
+  *split_tile = 0;
+  *zchunk2 = 0;
+  auto makespan = [&](int ka, int zc2) {
+    std::priority_queue<long, std::vector<long>, std::greater<long>> q;
+    for (int i = 0; i < sms; ++i) q.push(0);
+    auto run = [&](int tiles, int c) {
+      for (int z0 = 0; z0 < nz; z0 += c) {
+        const long len = std::min(c, nz - z0) + halo;
+        for (int t = 0; t < tiles; ++t) {
+          const long f = q.top();
+          q.pop();
+          q.push(f + len);
+        }
+      }
+    };
+    run(ka, zc);
+    if (zc2 > 0) run(ntiles - ka, zc2);
+    long m = 0;
+    for (; !q.empty(); q.pop()) m = std::max(m, q.top());
+    return m;
+  };
+  const long base = makespan(ntiles, 0);
+  long best = base;
+  const int rmax = std::min(ntiles, 2 * sms), rstep = std::max(1, sms / 64);
+  for (int parts = 2; parts <= 4; ++parts) {
+    const int zc2 = (zc + parts - 1) / parts;
+    if (zc2 < 8) break;
+    for (int r = rstep; r <= rmax; r += rstep) {
+      const long m = makespan(ntiles - r, zc2);
+      if (m < best) {
+        best = m;
+        *split_tile = ntiles - r;
+        *zchunk2 = zc2;
+      }
+    }
+  }
+  if (best * 100 > base * 98) {
+    *split_tile = 0;
+    *zchunk2 = 0;
+  }
+}
+
+// The split for a two-step launch of this handle (cached per tile and chunk).
+void tv_split_for(rihv_ctx* h, bool final, int zc, int* split_tile, int* zchunk2) {
+  auto& c = h->tv_split[final ? 1 : 0];
+  if (c.zchunk != zc) {
+    const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
+    const int ntiles = ((h->nx + tx - 1) / tx) * ((h->ny + ty - 1) / ty);
+    tv_choose_split(ntiles, h->nz, zc, final ? 4 : 3, h->sms, &c.split_tile, &c.zchunk2);
+    c.zchunk = zc;
+  }
+  *split_tile = c.split_tile;
+  *zchunk2 = c.zchunk2;
+}
+
 // Planes per z-chunk of a TV launch when none was tuned (final: the
 // fused-finalize launch's tile).
 int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false) {
@@ -533,8 +603,17 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
                    ? std::min(h->opt.tv_zchunk, h->nz)
                    : ((fused && last) ? zc_final
                                       : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32)));
-    if (fused && last && (tv_final_ctas(h->nx, h->ny, h->nz, a.zchunk) > h->fin_ctas ||
-                          a.zchunk > kTvMaxChunk))
+    // two-step launches: shorter z-chunks for the last tiles where that fills
+    // the last wave (not for the other launches of a batched graph, whose
+    // branches fill the GPU together; the fused-final launch's split depends
+    // only on the shape, so a batched solve keeps its restart-product order)
+    a.split_tile = 0;
+    a.zchunk2 = 0;
+    if (n == 2 && h->opt.tv_split && ((fused && last) || !h->batch_chunks))
+      tv_split_for(h, fused && last, a.zchunk, &a.split_tile, &a.zchunk2);
+    if (fused && last &&
+        (tv2_ctas(h->nx, h->ny, h->nz, true, a.zchunk, a.split_tile, a.zchunk2) > h->fin_ctas ||
+         a.zchunk > kTvMaxChunk))
       return fail(h, RIHV_ERR_INVALID_ARG, "z-chunk outside the fused finalize's range");
     a.tm_v = tm_v[b];
     for (int c = 0; c < 3; ++c) {
@@ -899,6 +978,7 @@ void rihv_default_options(rihv_options* o) {
   o->tv_zchunk = 0;
   o->fft_rows_per_cta = 0;
   o->tv_fgp = 0;
+  o->tv_split = 1;
   o->solver = 0;
 }
 
@@ -1077,7 +1157,8 @@ rihv_status rihv_set_options(rihv_handle h, const rihv_options* o) {
       (o->fft_rows_per_cta != 0 && o->fft_rows_per_cta != 1 && o->fft_rows_per_cta != 2 &&
        o->fft_rows_per_cta != 4 && o->fft_rows_per_cta != 8) ||
       (o->fft_rows_per_cta != 0 && h->ny % o->fft_rows_per_cta != 0) ||
-      (o->tv_fgp != 0 && o->tv_fgp != 1) || (o->solver != 0 && o->solver != 1))
+      (o->tv_fgp != 0 && o->tv_fgp != 1) || (o->solver != 0 && o->solver != 1) ||
+      (o->tv_split != 0 && o->tv_split != 1))
     return fail(h, RIHV_ERR_INVALID_ARG, "invalid options");
   // scratch of the optional iterations is allocated here, not inside a solve
   // (which may be being captured into a graph)
@@ -1449,7 +1530,7 @@ static bool same_options(const rihv_options& a, const rihv_options& o) {
          a.tv_steps_per_launch == o.tv_steps_per_launch && a.fuse_finalize == o.fuse_finalize &&
          a.f_star == o.f_star && a.tol == o.tol && a.skip_empty_planes == o.skip_empty_planes &&
          a.tv_zchunk == o.tv_zchunk && a.fft_rows_per_cta == o.fft_rows_per_cta &&
-         a.tv_fgp == o.tv_fgp && a.solver == o.solver;
+         a.tv_fgp == o.tv_fgp && a.solver == o.solver && a.tv_split == o.tv_split;
 }
 
 // Captures `fn` (enqueueing on h's stream, switched to `st` meanwhile) into a
@@ -1765,6 +1846,21 @@ static double time_ms(rihv_ctx* h, const std::function<rihv_status()>& fn, int r
   if (t.empty()) return 1e30;
   std::sort(t.begin(), t.end());
   return t[t.size() / 2];
+}
+
+rihv_status rihv_tv_schedule(rihv_handle h, int final, int* out3) {
+  if (!h || !out3 || (final != 0 && final != 1)) return fail(h, RIHV_ERR_INVALID_ARG, "invalid arguments");
+  const int zc = h->opt.tv_zchunk > 0
+                     ? std::min(h->opt.tv_zchunk, h->nz)
+                     : (final ? tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true)
+                              : (h->tv_zchunk > 0 ? h->tv_zchunk
+                                                  : tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms)));
+  int split = 0, zc2 = 0;
+  if (h->opt.tv_split) tv_split_for(h, final != 0, zc, &split, &zc2);
+  out3[0] = zc;
+  out3[1] = split;
+  out3[2] = zc2;
+  return RIHV_OK;
 }
 
 rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen) {

@@ -160,6 +160,12 @@ struct TvArgs {
   int* err;            // set to 1 if a bounded wait gave up
   int nx, ny, nz, dims;
   int zchunk;
+  // Two-step kernel only: with zchunk2 > 0 the tiles from split_tile on are
+  // cut into z-chunks of zchunk2 planes and launched after the others, so
+  // that shorter CTAs fill the last wave; zchunk2 = 0: every tile in
+  // z-chunks of zchunk planes.
+  int split_tile;
+  int zchunk2;
   float mu;            // t_tv
   float step;          // 1 / (4 dims mu)
   // Fused finalize (the last two-step launch of a prox writes x = soft(v -
@@ -189,6 +195,8 @@ struct TvArgs {
 // final (two-step launches only): fused finalize, no dual output.
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s,
                            bool final = false, bool fgp = false);
+// CTAs of a two-step launch with that z-chunking (final: the fused-finalize tile).
+int tv2_ctas(int nx, int ny, int nz, bool final, int zchunk, int split_tile, int zchunk2);
 // Box of box_rows x box_cols complex elements: (kTvBoxH1, kTvBoxW) for the
 // one-step kernel, (kTv2BoxH, kTv2BoxW) for the two-step kernel.
 cudaError_t make_volume_tmap(CUtensorMap* tm, const void* base, int nx, int ny, int nz,

@@ -32,6 +32,8 @@
 // restart flag on the device, so no scalar crosses to the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "rihv_internal.cuh"
 
 namespace rihv {
@@ -499,10 +501,27 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
   Row* XP1 = XU0 + 2;
   Row* XU1 = XU0 + 4;
   Row* XP2 = XU0 + 6;                           // FINAL only
-  const int zc0 = blockIdx.z * a.zchunk;
-  const int zc1 = min(a.nz, zc0 + a.zchunk);
+  // CTA -> (tile, z-chunk), 1D grid: tiles [0, ka) in z-chunks of zchunk
+  // planes, then tiles [ka, ntiles) in z-chunks of zchunk2, chunk-major within
+  // each part (x-adjacent tiles launch together). Without a split this is the
+  // order of an (x tiles, y tiles, z-chunks) grid.
+  const int tiles_x = (a.nx + TXk - 1) / TXk;
+  const int ntiles = tiles_x * ((a.ny + TYk - 1) / TYk);
+  const int ka = a.zchunk2 > 0 ? min(a.split_tile, ntiles) : ntiles;
+  const int ctas_a = ka * ((a.nz + a.zchunk - 1) / a.zchunk);
+  int tile, zc0, zc1;
+  if (static_cast<int>(blockIdx.x) < ctas_a) {
+    tile = blockIdx.x % ka;
+    zc0 = (blockIdx.x / ka) * a.zchunk;
+    zc1 = min(a.nz, zc0 + a.zchunk);
+  } else {
+    const int b2 = blockIdx.x - ctas_a, kb = ntiles - ka;
+    tile = ka + b2 % kb;
+    zc0 = (b2 / kb) * a.zchunk2;
+    zc1 = min(a.nz, zc0 + a.zchunk2);
+  }
   Ring ring{smem, reinterpret_cast<unsigned long long*>(smem + Layout::kBarOffset), zc0 - 2 - L};
-  const int i0 = blockIdx.x * TXk, j0 = blockIdx.y * TYk;
+  const int i0 = (tile % tiles_x) * TXk, j0 = (tile / tiles_x) * TYk;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int gx0 = i0 - X0 + 2 * lane, gy = j0 - (Y0 - 1) + w;   // element e at x = gx0 + e
   const int by = w + 1;                                 // own row in the box
@@ -768,8 +787,8 @@ __global__ void __launch_bounds__(32 * (FINAL ? kTv2WarpsF : kTv2Warps), 1)
     // fixed-order sum over the CTAs by the last one, which updates t and beta
     const double bs = block_sum(static_cast<double>(dot_hi) + static_cast<double>(dot_lo));
     // (block_sum's barriers also publish occ_s)
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblk = gridDim.x;
+    const int bid = blockIdx.x;
     if (OCC) {
       if (tid < zc1 - zc0 && occ_s[tid]) {
         a.occ[zc0 + tid] = 1;
@@ -982,6 +1001,14 @@ int stream_grid(size_t nvox) {
 
 }  // namespace
 
+int tv2_ctas(int nx, int ny, int nz, bool final, int zchunk, int split_tile, int zchunk2) {
+  const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
+  const int ntiles = ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+  const int ka = zchunk2 > 0 ? std::min(std::max(split_tile, 0), ntiles) : ntiles;
+  const int cb = zchunk2 > 0 ? (ntiles - ka) * ((nz + zchunk2 - 1) / zchunk2) : 0;
+  return ka * ((nz + zchunk - 1) / zchunk) + cb;
+}
+
 cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t s, bool final,
                            bool fgp) {
   if (nsteps == 2 && (a.nx & 1)) return cudaErrorInvalidValue;   // pairs of x positions
@@ -990,6 +1017,7 @@ cudaError_t launch_tv_step(bool first, int nsteps, const TvArgs& a, cudaStream_t
   const int tx = nsteps == 2 ? (final ? kTv2TxF : TX2) : TX;
   const int ty = nsteps == 2 ? (final ? kTv2TyF : kTv2Ty) : TY;
   dim3 grid((a.nx + tx - 1) / tx, (a.ny + ty - 1) / ty, (a.nz + a.zchunk - 1) / a.zchunk);
+  if (nsteps == 2) grid = dim3(tv2_ctas(a.nx, a.ny, a.nz, final, a.zchunk, a.split_tile, a.zchunk2));
   const bool fista = a.fin_mode == FIN_FISTA;
   auto kern = nsteps == 2
                   ? (final ? (fista ? (a.occ ? (first ? k_tv_step2<true, true, kFinFistaOcc>

@@ -25,7 +25,7 @@ EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stre
            "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
            "rihv_solve", "rihv_detect", "rihv_detect_coo", "rihv_fasta_steps", "rihv_set_profiling", "rihv_stage_times",
            "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
-           "rihv_batch_destroy", "rihv_autotune"]
+           "rihv_batch_destroy", "rihv_autotune", "rihv_tv_schedule"]
 
 STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup",
           "tv_first", "tv_mid", "tv_final"]
@@ -53,7 +53,7 @@ class Options(ctypes.Structure):
                 ("f_star", ctypes.c_double), ("tv_steps_per_launch", ctypes.c_int),
                 ("fuse_finalize", ctypes.c_int), ("skip_empty_planes", ctypes.c_int),
                 ("tv_zchunk", ctypes.c_int), ("fft_rows_per_cta", ctypes.c_int),
-                ("tv_fgp", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("tv_fgp", ctypes.c_int), ("solver", ctypes.c_int), ("tv_split", ctypes.c_int)]
 
 
 class Particle(ctypes.Structure):
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_batch_destroy": (i, [H]),
         "rihv_batch_iterations": (i, [H, ctypes.POINTER(i)]),
         "rihv_autotune": (i, [H, ctypes.c_char_p, ctypes.POINTER(i)]),
+        "rihv_tv_schedule": (i, [H, i, ctypes.POINTER(i)]),
         "rihv_coo_compact": (i, [H, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "rihv_coo_expand": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, vp]),
@@ -310,6 +311,17 @@ class Rihv:
         return tuple(out)
 
     autotune = rihv_autotune
+
+    def rihv_tv_schedule(self, final=False):
+        """(planes per z-chunk, split tile, planes per z-chunk from the split
+        tile on, 0 without a split) of the two-step TV launches of a solve:
+        final=False for the launches reading the dual, True for the fused
+        finalize."""
+        out = (ctypes.c_int * 3)()
+        self._check(self.L.rihv_tv_schedule(self.h, int(bool(final)), out), self.h)
+        return tuple(out)
+
+    tv_schedule = rihv_tv_schedule
 
     # -- profiling ----------------------------------------------------------
     def rihv_selftest_bounded_wait(self, polls=4096):
