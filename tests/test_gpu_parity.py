@@ -266,6 +266,17 @@ def test_solve_is_deterministic_and_resumable():
     xh = np.zeros(op.shape, np.complex64)
     h.solve(b, w.lam_l1, w.lam_tv, 3, xh, x0=x1)
     assert np.isfinite(xh).all() and np.abs(xh).sum() > 0
+    # host buffers that start inside a page (the library reads one byte of
+    # every page they span before the copies) give the device result exactly
+    n = int(np.prod(op.shape))
+    raw = bytearray(8 * n + 4096 + 24)
+    xo = np.frombuffer(raw, np.complex64, count=n, offset=24).reshape(op.shape)
+    x0h = np.frombuffer(bytearray(8 * n + 40), np.complex64, count=n, offset=40).reshape(op.shape)
+    x0h[...] = x1.cpu().numpy()
+    xd = torch.empty_like(x1)
+    h.solve(b, w.lam_l1, w.lam_tv, 3, xo, x0=x0h)
+    h.solve(b, w.lam_l1, w.lam_tv, 3, xd, x0=x1)
+    assert np.array_equal(xo, xd.cpu().numpy()) and np.array_equal(xo, xh)
 
 
 def test_ista_single_iteration_matches_oracle():
