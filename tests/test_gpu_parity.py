@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs.
 
-Tolerances (north star of this project): relative L2 <= 1e-5 per operator
+Tolerances (the parity bar of this project): relative L2 <= 1e-5 per operator
 application (forward, adjoint, one fused-lasso prox call), <= 1e-3 on the final
 volume after a fixed number of FISTA iterations, identical detections with
 centroids within 0.5 voxel.
