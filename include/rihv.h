@@ -279,6 +279,13 @@ rihv_status rihv_autotune(rihv_handle h, const char* cache_path, int* chosen_or_
  * (option tv_split). Host-only; no device work. */
 rihv_status rihv_tv_schedule(rihv_handle h, int final, int* out3);
 
+/* The split rule itself, without a handle or a device (not in the paper):
+ * for an nx x ny x nz volume, a two-step TV launch (final = 1: the
+ * fused-finalize tile) with z-chunks of `zchunk` planes on `sms` SMs, one
+ * CTA per SM. out2 receives {split_tile, planes per z-chunk from split_tile
+ * on}, {0, 0} when equal z-chunks are kept. Host computation only. */
+rihv_status rihv_tv_split_plan(int nx, int ny, int nz, int final, int zchunk, int sms, int* out2);
+
 /* Steps of the last rihv_solve run with the FASTA-style solver (option
  * solver = 1; not in the paper beyond its naming FASTA): the accepted step
  * size of every iteration, in order, into taus (host, first `capacity`

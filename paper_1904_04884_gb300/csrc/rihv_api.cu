@@ -1848,6 +1848,15 @@ static double time_ms(rihv_ctx* h, const std::function<rihv_status()>& fn, int r
   return t[t.size() / 2];
 }
 
+rihv_status rihv_tv_split_plan(int nx, int ny, int nz, int final, int zchunk, int sms, int* out2) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || zchunk <= 0 || sms <= 0 || !out2 || (final != 0 && final != 1))
+    return fail(nullptr, RIHV_ERR_INVALID_ARG, "invalid arguments");
+  const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
+  const int ntiles = ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+  tv_choose_split(ntiles, nz, std::min(zchunk, nz), final ? 4 : 3, sms, &out2[0], &out2[1]);
+  return RIHV_OK;
+}
+
 rihv_status rihv_tv_schedule(rihv_handle h, int final, int* out3) {
   if (!h || !out3 || (final != 0 && final != 1)) return fail(h, RIHV_ERR_INVALID_ARG, "invalid arguments");
   const int zc = h->opt.tv_zchunk > 0

@@ -25,7 +25,7 @@ EXPORTS = ["rihv_default_options", "rihv_create", "rihv_destroy", "rihv_set_stre
            "rihv_set_options", "rihv_forward", "rihv_adjoint", "rihv_prox_fused_lasso",
            "rihv_solve", "rihv_detect", "rihv_detect_coo", "rihv_fasta_steps", "rihv_set_profiling", "rihv_stage_times",
            "rihv_step_size", "rihv_last_error", "rihv_batch_create", "rihv_batch_solve",
-           "rihv_batch_destroy", "rihv_autotune", "rihv_tv_schedule"]
+           "rihv_batch_destroy", "rihv_autotune", "rihv_tv_schedule", "rihv_tv_split_plan"]
 
 STAGES = ["forward", "adjoint", "tv", "finalize", "objective", "detect", "setup",
           "tv_first", "tv_mid", "tv_final"]
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "rihv_batch_iterations": (i, [H, ctypes.POINTER(i)]),
         "rihv_autotune": (i, [H, ctypes.c_char_p, ctypes.POINTER(i)]),
         "rihv_tv_schedule": (i, [H, i, ctypes.POINTER(i)]),
+        "rihv_tv_split_plan": (i, [i, i, i, i, i, i, ctypes.POINTER(i)]),
         "rihv_coo_compact": (i, [H, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "rihv_coo_expand": (i, [H, vp, vp, vp, vp, ctypes.c_longlong, vp]),
@@ -400,6 +401,19 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def rihv_tv_split_plan(nx, ny, nz, final, zchunk, sms=152):
+    """(split tile, planes per z-chunk from it on) that the library's split
+    rule gives a two-step TV launch of an nx x ny x nz volume with z-chunks of
+    `zchunk` planes on `sms` SMs; (0, 0) keeps equal chunks. Host only."""
+    L = load_library()
+    out = (ctypes.c_int * 2)()
+    st = L.rihv_tv_split_plan(int(nx), int(ny), int(nz), int(final), int(zchunk), int(sms), out)
+    if st != 0:
+        msg = L.rihv_last_error(None)
+        raise RihvError(st, msg.decode() if msg else "rihv_tv_split_plan failed")
+    return tuple(out)
 
 
 def rihv_prox_fused_lasso_noalloc(v, x_out, nz, ny, nx, tv_dims, t_l1, t_tv, inner_iters,
