@@ -12,7 +12,7 @@ import torch
 
 from oracle import rihv_oracle as O
 from paper_1904_04884_gb300 import synth
-from paper_1904_04884_gb300.rihv import Batch, Rihv
+from paper_1904_04884_gb300.rihv import Batch, Rihv, rihv_tv_split_plan
 
 pytestmark = pytest.mark.gpu
 
@@ -40,9 +40,11 @@ def volume(seed):
 
 def test_the_schedule_splits_on_this_shape():
     h = handle()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     for final in (False, True):
         zc, split, zc2 = h.tv_schedule(final)
         assert 0 < zc2 < zc and 0 < split, (final, zc, split, zc2)
+        assert (split, zc2) == rihv_tv_split_plan(NX, NY, NZ, final, zc, sms)
     h.set_options(tv_split=0)
     assert h.tv_schedule(False)[2] == 0 and h.tv_schedule(True)[2] == 0
     h.close()
