@@ -412,6 +412,34 @@ int tv_final_ctas(int nx, int ny, int nz, int zchunk) {
   return ((nx + kTv2TxF - 1) / kTv2TxF) * ((ny + kTv2TyF - 1) / kTv2TyF) * ((nz + zchunk - 1) / zchunk);
 }
 
+
+// Planes per z-chunk of a TV launch when none was tuned (final: the
+// fused-finalize launch's tile).
+int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false) {
+  if (nsteps != 2) return 32;
+  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks (zc + 4 for
+  // the fused final launch, one more plane of z halo). The cost of a chunk
+  // size is (waves, rounded up) x (ticks per chunk), over chunks in [8, 256].
+  // Every chunk also reads its z halo again, which this count leaves out, so
+  // among the chunks within 3 % of the lowest cost the largest is taken.
+  const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
+  const int halo = final ? 4 : 3;
+  const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+  auto cost = [&](int c) {
+    const long ctas = tiles * ((nz + c - 1) / c);
+    return ((ctas + sms - 1) / sms) * (c + halo);
+  };
+  const int cmax = nz < kTvMaxChunk ? nz : kTvMaxChunk;
+  const int cmin = nz < 8 ? nz : 8;
+  long lowest = -1;
+  for (int c = cmin; c <= cmax; ++c)
+    if (lowest < 0 || cost(c) < lowest) lowest = cost(c);
+  int best = cmin;
+  for (int c = cmin; c <= cmax; ++c)
+    if (cost(c) * 100 <= lowest * 103) best = c;
+  return best;
+}
+
 // Split of a two-step TV launch (TvArgs::split_tile, zchunk2). With one CTA
 // per SM, equal z-chunks leave the last wave partly idle (at 1024x1024x256,
 // 1,152 CTAs fill 7.6 waves). Model: a CTA of c planes takes c + halo plane
@@ -463,6 +491,24 @@ void tv_choose_split(int ntiles, int nz, int zc, int halo, int sms, int* split_t
   }
 }
 
+// Planes per z-chunk of a TV launch of n dual steps in a prox of `per` steps
+// per launch: the option, else (fused-final launch) its own tile's default,
+// else the tuned chunk, else the default of the launch's tile (one-step
+// launches: 32). In a batched graph the branches run concurrently, so the
+// two-step launches take the largest chunk (fewest halo planes read twice)
+// rather than the one that fills the waves of a lone launch. The fused-final
+// launch keeps the lone-solve chunk: its restart-product partials follow the
+// chunking, and with them a batched solve stays bitwise equal to a single one
+// (no other TV result depends on the chunk).
+int tv_launch_zchunk(const rihv_ctx* h, int n, int per, bool fused_last) {
+  if (h->opt.tv_zchunk > 0) return std::min(h->opt.tv_zchunk, h->nz);
+  if (fused_last) return tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true);
+  if (h->tv_zchunk > 0) return h->tv_zchunk;
+  if (n != per) return 32;
+  return (h->batch_chunks && per == 2) ? std::min(h->nz, kTvMaxChunk)
+                                       : tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
+}
+
 // The split for a two-step launch of this handle (cached per tile and chunk).
 void tv_split_for(rihv_ctx* h, bool final, int zc, int* split_tile, int* zchunk2) {
   auto& c = h->tv_split[final ? 1 : 0];
@@ -474,33 +520,6 @@ void tv_split_for(rihv_ctx* h, bool final, int zc, int* split_tile, int* zchunk2
   }
   *split_tile = c.split_tile;
   *zchunk2 = c.zchunk2;
-}
-
-// Planes per z-chunk of a TV launch when none was tuned (final: the
-// fused-finalize launch's tile).
-int tv_default_zchunk(int nx, int ny, int nz, int nsteps, int sms, bool final = false) {
-  if (nsteps != 2) return 32;
-  // One CTA per SM; a chunk of zc planes takes zc + 3 plane ticks (zc + 4 for
-  // the fused final launch, one more plane of z halo). The cost of a chunk
-  // size is (waves, rounded up) x (ticks per chunk), over chunks in [8, 256].
-  // Every chunk also reads its z halo again, which this count leaves out, so
-  // among the chunks within 3 % of the lowest cost the largest is taken.
-  const int tx = final ? kTv2TxF : kTv2Tx, ty = final ? kTv2TyF : kTv2Ty;
-  const int halo = final ? 4 : 3;
-  const long tiles = static_cast<long>((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
-  auto cost = [&](int c) {
-    const long ctas = tiles * ((nz + c - 1) / c);
-    return ((ctas + sms - 1) / sms) * (c + halo);
-  };
-  const int cmax = nz < kTvMaxChunk ? nz : kTvMaxChunk;
-  const int cmin = nz < 8 ? nz : 8;
-  long lowest = -1;
-  for (int c = cmin; c <= cmax; ++c)
-    if (lowest < 0 || cost(c) < lowest) lowest = cost(c);
-  int best = cmin;
-  for (int c = cmin; c <= cmax; ++c)
-    if (cost(c) * 100 <= lowest * 103) best = c;
-  return best;
 }
 
 // K steps of the accelerated dual (FGP), one per launch: the step at the
@@ -566,16 +585,6 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
   a.ny = h->ny;
   a.nz = h->nz;
   a.dims = h->opt.tv_dims;
-  // In a batched graph the branches run concurrently, so the two-step
-  // launches take the largest chunk (fewest halo planes read twice) rather
-  // than the one that fills the waves of a lone launch. The fused-final
-  // launch keeps the lone-solve chunk: its restart-product partials follow
-  // the chunking, and with them a batched solve stays bitwise equal to a
-  // single one (no other TV result depends on the chunk).
-  const int zc_auto = (h->batch_chunks && per == 2)
-                          ? std::min(h->nz, kTvMaxChunk)
-                          : tv_default_zchunk(h->nx, h->ny, h->nz, per, h->sms);
-  const int zc_final = tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true);
   a.mu = mu;
   a.step = 1.f / (4.f * a.dims * mu);
   if (fused) {
@@ -599,10 +608,7 @@ rihv_status tv_steps(rihv_ctx* h, const float2* v, float mu, int k, float2* cons
     const bool last = done + n == k;
     const int b = n == 2 ? ((fused && last) ? 2 : 1) : 0;
     // the fused-finalize launch has its own tile, so its own default chunk
-    a.zchunk = h->opt.tv_zchunk > 0
-                   ? std::min(h->opt.tv_zchunk, h->nz)
-                   : ((fused && last) ? zc_final
-                                      : (h->tv_zchunk > 0 ? h->tv_zchunk : (n == per ? zc_auto : 32)));
+    a.zchunk = tv_launch_zchunk(h, n, per, fused && last);
     // two-step launches: shorter z-chunks for the last tiles where that fills
     // the last wave (not for the other launches of a batched graph, whose
     // branches fill the GPU together; the fused-final launch's split depends
@@ -1859,11 +1865,7 @@ rihv_status rihv_tv_split_plan(int nx, int ny, int nz, int final, int zchunk, in
 
 rihv_status rihv_tv_schedule(rihv_handle h, int final, int* out3) {
   if (!h || !out3 || (final != 0 && final != 1)) return fail(h, RIHV_ERR_INVALID_ARG, "invalid arguments");
-  const int zc = h->opt.tv_zchunk > 0
-                     ? std::min(h->opt.tv_zchunk, h->nz)
-                     : (final ? tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms, true)
-                              : (h->tv_zchunk > 0 ? h->tv_zchunk
-                                                  : tv_default_zchunk(h->nx, h->ny, h->nz, 2, h->sms)));
+  const int zc = tv_launch_zchunk(h, 2, 2, final != 0);
   int split = 0, zc2 = 0;
   if (h->opt.tv_split) tv_split_for(h, final != 0, zc, &split, &zc2);
   out3[0] = zc;
