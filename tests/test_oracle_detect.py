@@ -61,5 +61,21 @@ def test_threshold_is_strict_and_float32():
     assert m[0, 0, 0] and not m[0, 3, 3] and m[0, 3, 2]
 
 
+def test_threshold_decision_rounds_each_operation_to_float32():
+    """A voxel whose float32 and float64 decisions differ. max|x| = 1 and
+    rel = 2^-7 give the threshold square 2^-14 exactly in either precision.
+    The voxel 2^-7 + 2^-20 i has |x|^2 = 2^-14 + 2^-40: above the threshold
+    in float64, but in float32 the sum re*re + im*im rounds to 2^-14 (2^-40
+    is below half an ulp of 2^-14, which is 2^-38), not above it. The
+    decision is the float32 one (strict >, each operation rounded)."""
+    x = np.zeros((1, 2, 2), complex)
+    x[0, 0, 0] = 1.0
+    x[0, 1, 1] = 2.0 ** -7 + 1j * 2.0 ** -20
+    x[0, 1, 0] = 2.0 ** -7 + 1j * 2.0 ** -18      # 2^-36 survives the float32 sum
+    assert abs(x[0, 1, 1]) ** 2 > 2.0 ** -14
+    m = O.detection_mask(x, 2.0 ** -7)
+    assert m[0, 0, 0] and not m[0, 1, 1] and m[0, 1, 0]
+
+
 def test_empty_detection():
     assert O.detect(np.zeros((2, 3, 4)), 0.1, 5) == []

@@ -71,3 +71,14 @@ def test_pool_upsample_adjoints():
     y = rng.standard_normal((4, 6, 8, 3))
     assert abs(np.sum(U.upsample2(g) * y) - np.sum(g * U.upsample2_grad(y))) < 1e-12
     np.testing.assert_allclose(U.avgpool2(np.ones((2, 2, 2, 1))), np.ones((1, 1, 1, 1)))
+
+
+def test_relu_and_upsample_by_hand():
+    """ReLU keeps positive values and zeroes the rest; nearest upsampling
+    copies each voxel into its 2 x 2 x 2 cell."""
+    x = np.array([-2.0, -0.0, 0.5, 3.0]).reshape(1, 1, 4, 1)
+    np.testing.assert_array_equal(U.relu(x).ravel(), [0.0, 0.0, 0.5, 3.0])
+    g = np.arange(2.0).reshape(1, 1, 2, 1)
+    up = U.upsample2(g)
+    assert up.shape == (2, 2, 4, 1)
+    np.testing.assert_array_equal(up[:, :, :, 0], np.array([[[0, 0, 1, 1]] * 2] * 2))
