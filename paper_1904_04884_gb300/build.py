@@ -50,7 +50,9 @@ def up_to_date() -> bool:
         return False
     t = os.path.getmtime(LIB)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    deps.append(os.path.join(HERE, "..", "include", "rihv.h"))
+    inc = os.path.join(HERE, "..", "include")
+    if os.path.isdir(inc):
+        deps += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     deps.append(os.path.abspath(__file__))
     return all(os.path.getmtime(d) <= t for d in deps if os.path.exists(d))
 
