@@ -99,6 +99,20 @@ CORE = [
  ("coo bytes", "return 24 * nnz", "return 16 * nnz"),
  ("freq pitch", "fx = np.fft.fftfreq(optics.nx, d=optics.pitch)", "fx = np.fft.fftfreq(optics.nx, d=2 * optics.pitch)"),
  ("evanescent keep", "return np.where(propagating, np.exp(2j * np.pi * z * kappa), 0.0)", "return np.exp(2j * np.pi * z * kappa)"),
+ ("meshgrid swap", 'return np.meshgrid(fy, fx, indexing="ij")', 'return np.meshgrid(fx, fy, indexing="ij")[::-1]'),
+ ("data term real part", "return float(np.vdot(r, r).real)", "return float(np.sum(r.real ** 2))"),
+ ("detect first last", "np.minimum.at(first, lab, idx)", "np.maximum.at(first, lab, idx)"),
+ ("coo offsets", "offsets[k + 1] = offsets[k] + len(j)", "offsets[k + 1] = len(j)"),
+ ("proj radius", "scale = 1.0 / np.maximum(1.0, norm)", "scale = 1.0 / np.maximum(0.5, norm)"),
+ ("soft real modulus", "    mag = np.abs(u)\n    with", "    mag = np.abs(u.real)\n    with"),
+ ("tv_norm dims", "dx, dy, dzz = grad_op(x, dims)\n    return float", "dx, dy, dzz = grad_op(x, 3)\n    return float"),
+ ("fgp keep p_prev", "        p_prev, t = p, t_next", "        t = t_next"),
+ ("fasta grad at old", "g_new = grad_data(x_new, b, optics)", "g_new = grad_data(x, b, optics)"),
+ ("fasta hist old f", "f_hist.append(f_new)", "f_hist.append(f_hist[-1])"),
+ ("fista ista keeps y", "            t_next = 1.0\n            y_next = x.copy()\n        x_prev", "            t_next = 1.0\n            y_next = y\n        x_prev"),
+ ("adjoint spectrum once", "out[j] = np.fft.ifft2(np.conj(transfer_function(optics, z)) * spectrum)", "out[j] = np.fft.ifft2(np.conj(transfer_function(optics, z)) * spectrum) / optics.nz"),
+ ("forward skips last plane", "    for j, z in enumerate(optics.depths()):\n        out += propagate", "    for j, z in enumerate(optics.depths()[:-1]):\n        out += propagate"),
+ ("detect centroid z", "sz = np.bincount(lab, weights=wv * kz, minlength=n)", "sz = np.bincount(lab, weights=wv * jy, minlength=n)"),
 ]
 
 UNET = [

@@ -59,7 +59,9 @@ def test_lasso_kkt_conditions_at_convergence():
 
 
 def test_ista_monotone_without_tv():
-    """ISTA with an exact prox never increases the objective."""
+    """ISTA with an exact prox never increases the objective. ISTA keeps no
+    state between iterations (each step starts from the last iterate), so 15
+    iterations in one call equal 15 chained single-iteration calls."""
     b = _hologram(SMALL, 3)
     vals = [O.objective(np.zeros(SMALL.shape), b, SMALL, 0.3, 0.0)]
     x = None
@@ -67,6 +69,9 @@ def test_ista_monotone_without_tv():
         x, _ = O.fista(b, SMALL, 0.3, 0.0, iters=1, n_inner=0, accelerate=False, x0=x)
         vals.append(O.objective(x, b, SMALL, 0.3, 0.0))
     assert all(v1 <= v0 + 1e-12 * abs(v0) for v0, v1 in zip(vals, vals[1:]))
+    assert vals[-1] < vals[1] - 1e-3 * abs(vals[1])
+    x15, _ = O.fista(b, SMALL, 0.3, 0.0, iters=15, n_inner=0, accelerate=False)
+    np.testing.assert_array_equal(x15, x)
 
 
 def test_ista_monotone_with_converged_tv_prox():
