@@ -42,7 +42,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-TV_PROFILE = os.path.join(ROOT, "profiles", "tv_step_traffic.json")
+TV_PROFILE = os.path.join(ROOT, "profiles", "tv_step2_traffic_solve_512x512x128.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
