@@ -13,7 +13,7 @@ roofline: the TV dual-step kernel (the dominant kernel), from CUDA events the
          last timed step; algorithmic bytes 56 per voxel for a launch reading p.
 mid    : the same measurement on the 512 x 512 x 128 workload (200 iterations).
 cpu_baseline: the FP64 oracle, as it stands, on the host cores: one process
-         per core (spawned), each solving its own 2-plane slab of the workload,
+         per core (spawned), each solving its own one-plane slab of the workload,
          and the same on one core.
 time_to_tolerance: per-hologram time to F*(1+1e-3) on 20 held-out 256x256x64
          samples: plain FISTA, the learned warm start, batching, and both,
@@ -21,6 +21,10 @@ time_to_tolerance: per-hologram time to F*(1+1e-3) on 20 held-out 256x256x64
 batched: the time-resolved 64-frame sequence of mixed sizes (256^2 x 64,
          512^2 x 128, 768^2 x 192) as batched CUDA graphs against one frame
          at a time.
+library_baseline: the same FISTA iteration on the same workload written
+         with PyTorch operators (cuFFT plane transforms, stored transfer
+         functions, one element-wise kernel per operation), the way the
+         paper describes its own GPU code; two timed iterations.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank reconstructs its own hologram (independent work, no
@@ -61,7 +65,7 @@ def parse():
                         "1024x1024x256 it measured slower than the default tiles)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the secondary measurements (mid workload, time to tolerance, "
-                        "mixed-size sequence)")
+                        "mixed-size sequence, library baseline)")
     return p.parse_args()
 
 
@@ -425,6 +429,126 @@ def time_to_tolerance(n_seeds=20, tol=1e-3, max_iters=400):
             "speedup": plain / wb}
 
 
+class LibraryFista:
+    """The fused-lasso FISTA iteration built the way the paper describes its
+    own GPU code (Section 2, GPU implementation paragraph: a library FFT of
+    every plane, the plane's transfer function applied in the spectrum,
+    element-wise kernels for the rest), written with PyTorch operators:
+    cuFFT for the 2D transforms, one element-wise kernel per operation, the
+    transfer functions of all planes stored, the restart test read back to
+    the host every iteration. Same method and FP32 complex arithmetic as the
+    hand-written kernels, none of their fusion: a measured baseline for
+    them. Nothing in the library uses it."""
+
+    def __init__(self, w, device):
+        import math
+
+        import torch
+        self.t = torch
+        self.w = w
+        f64 = torch.float64
+        fx = torch.fft.fftfreq(w.nx, d=w.pitch, dtype=f64, device=device)
+        fy = torch.fft.fftfreq(w.ny, d=w.pitch, dtype=f64, device=device)
+        f2 = fy[:, None] ** 2 + fx[None, :] ** 2
+        prop = (w.wavelength ** 2) * f2 < 1.0
+        kappa = torch.sqrt(torch.where(prop, 1.0 / w.wavelength ** 2 - f2, torch.zeros_like(f2)))
+        self.H = torch.empty(w.shape, dtype=torch.complex64, device=device)
+        amp = prop.to(f64)
+        for j in range(w.nz):          # plane by plane: FP64 phase modulo one cycle
+            cyc = torch.remainder((w.z0 + j * w.dz) * kappa, 1.0)
+            self.H[j] = torch.polar(amp, 2.0 * math.pi * cyc).to(torch.complex64)
+        lip = 2.0 * float((self.H.abs() ** 2).sum(0).max())
+        self.tau = 1.0 / lip if lip > 0 else 0.0
+
+    def forward(self, x):
+        fft = self.t.fft
+        return fft.ifft2((self.H * fft.fft2(x)).sum(0))
+
+    def adjoint(self, r):
+        fft = self.t.fft
+        return fft.ifft2(self.H.conj() * fft.fft2(r)[None])
+
+    def _d(self, u, dims):
+        t = self.t
+        dx, dy, dz = t.zeros_like(u), t.zeros_like(u), t.zeros_like(u)
+        dx[:, :, :-1] = u[:, :, 1:] - u[:, :, :-1]
+        dy[:, :-1, :] = u[:, 1:, :] - u[:, :-1, :]
+        if dims == 3:
+            dz[:-1] = u[1:] - u[:-1]
+        return dx, dy, dz
+
+    def _dh(self, px, py, pz, dims):
+        out = self.t.zeros_like(px)
+        out[:, :, :-1] -= px[:, :, :-1]
+        out[:, :, 1:] += px[:, :, :-1]
+        out[:, :-1, :] -= py[:, :-1, :]
+        out[:, 1:, :] += py[:, :-1, :]
+        if dims == 3:
+            out[:-1] -= pz[:-1]
+            out[1:] += pz[:-1]
+        return out
+
+    def tv_prox(self, v, mu, k, dims):
+        """K dual gradient-projection steps from p = 0, then v - mu D^H p."""
+        t = self.t
+        if mu == 0.0 or k == 0:
+            return v.clone()
+        p = [t.zeros_like(v) for _ in range(3)]
+        step = 1.0 / (4.0 * dims * mu)
+        for _ in range(k):
+            g = self._d(v - mu * self._dh(*p, dims), dims)
+            p = [pc + step * gc for pc, gc in zip(p, g)]
+            norm = t.sqrt(sum(pc.real ** 2 + pc.imag ** 2 for pc in p))
+            s = 1.0 / t.clamp(norm, min=1.0)
+            p = [pc * s for pc in p]
+        return v - mu * self._dh(*p, dims)
+
+    def soft(self, u, kappa):
+        t = self.t
+        mag = u.abs()
+        s = t.where(mag > kappa, 1.0 - kappa / t.clamp(mag, min=1e-30), t.zeros_like(mag))
+        return u * s
+
+    def solve(self, b, lam_l1, lam_tv, iters, k, dims, x0=None):
+        """`iters` FISTA iterations (gradient restart on) from x0 or 0."""
+        t = self.t
+        tau = self.tau
+        x_prev = t.zeros(self.w.shape, dtype=t.complex64, device=self.H.device) if x0 is None \
+            else x0.clone()
+        y, tk = x_prev.clone(), 1.0
+        for _ in range(iters):
+            v = y - (2.0 * tau) * self.adjoint(self.forward(y) - b)
+            x = self.soft(self.tv_prox(v, tau * lam_tv, k, dims), tau * lam_l1)
+            t_next = (1.0 + (1.0 + 4.0 * tk * tk) ** 0.5) / 2.0
+            dx = x - x_prev
+            if float((dx.conj() * (y - x)).real.sum()) > 0.0:
+                t_next, y = 1.0, x.clone()
+            else:
+                y = x + ((tk - 1.0) / t_next) * dx
+            x_prev, tk = x, t_next
+        return x_prev
+
+
+def library_baseline(w, b, dev, iters=2):
+    """Voxel-iterations/s of `LibraryFista` on workload w (one untimed
+    iteration first), CUDA events on the current stream."""
+    import torch
+    lf = LibraryFista(w, dev)
+    bd = torch.from_numpy(np.asarray(b, np.float32)).to(dev).to(torch.complex64)
+    lf.solve(bd, w.lam_l1, w.lam_tv, 1, w.n_inner, w.tv_dims)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lf.solve(bd, w.lam_l1, w.lam_tv, iters, w.n_inner, w.tv_dims)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": w.nvox * iters / (ms / 1e3), "unit": "voxel-iter/s",
+            "ms_per_iteration": ms / iters, "iterations_timed": iters,
+            "what": "the same FISTA iteration with PyTorch operators: cuFFT plane transforms, "
+                    "stored transfer functions, one element-wise kernel per operation"}
+
+
 def mixed_sequence(frames=64, iters=50, slots=4):
     """The time-resolved mixed-size sequence: batched graphs against one frame
     at a time (paper_1904_04884_gb300.sequence)."""
@@ -577,7 +701,7 @@ def main():
     del x_dev, b_dev
     torch.cuda.empty_cache()
 
-    mid = ttt = batched = None
+    mid = ttt = batched = library = None
     if not args.no_extras and world == 1:
         if w.name != workloads.MID.name:
             mid = solve_rate(workloads.MID, dev)
@@ -585,6 +709,12 @@ def main():
         ttt = time_to_tolerance()
         torch.cuda.empty_cache()
         batched = mixed_sequence()
+        torch.cuda.empty_cache()
+        try:
+            library = library_baseline(w, b, dev)
+        except Exception as e:       # a failed baseline must not cost the bench line
+            library = {"error": f"{type(e).__name__}: {e}"[:300]}
+        torch.cuda.empty_cache()
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -617,6 +747,7 @@ def main():
         "mid": mid,
         "time_to_tolerance": ttt,
         "batched": batched,
+        "library_baseline": library,
         "coo": coo,
         "clocks": clocks,
         "cpu_baseline": cpu,
